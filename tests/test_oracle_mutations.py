@@ -1,0 +1,135 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that the pins catch each one.
+
+Each mutation is a one-line edit of the oracle's own source text, executed as a fresh module; a pin
+set that a dropped term, a wrong sign, a wrong index or a transposed operand slips through would not
+pin anything, so every mutation must push at least one pin far above rounding.
+"""
+import sys
+import types
+
+import numpy as np
+import pytest
+
+from oracle import operator as O
+from oracle import solver as S
+from paper_0907_3261_gb300 import inputs as I
+import pins
+
+PIN_TOL = 1e-10
+
+
+def mutated_module(module, edits):
+    src = open(module.__file__).read()
+    for old, new in edits:
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    name = module.__name__ + "_mutated"
+    mod = types.ModuleType(name)
+    sys.modules[name] = mod          # dataclasses look their module up here
+    try:
+        exec(compile(src, module.__file__ + "[mutated]", "exec"), mod.__dict__)
+    finally:
+        del sys.modules[name]
+    return mod.__dict__
+
+
+OPERATOR_MUTATIONS = {
+    "swap_projectors": [('one - self.g[mu], up', 'one + self.g[mu], up'),
+                        ('one + self.g[mu], dn', 'one - self.g[mu], dn')],
+    "no_dagger_backward": [('_dag(U_back), psi', 'U_back, psi')],
+    "backward_link_at_x": [('U_back = self.U[self.lat.bwd[mu], mu]', 'U_back = self.U[:, mu]')],
+    "transpose_forward": [('"vab,vsbl->vsal", self.U[:, mu]', '"vba,vsbl->vsal", self.U[:, mu]')],
+    "backward_reads_forward": [('psi[self.lat.bwd[mu]])', 'psi[self.lat.fwd[mu]])')],
+    "hopping_sign": [('(psi) - self.kappa * self.hopping', '(psi) + self.kappa * self.hopping')],
+    "hopping_factor_two": [('(psi) - self.kappa * self.hopping',
+                            '(psi) - 2 * self.kappa * self.hopping')],
+    "gamma_t_sign": [('g[3, 0:2, 2:4] = np.eye(2)', 'g[3, 0:2, 2:4] = -np.eye(2)'),
+                     ('g[3, 2:4, 0:2] = np.eye(2)', 'g[3, 2:4, 0:2] = -np.eye(2)')],
+    "leaf_order": [('leaf1 = Um @ Un[x_pm]', 'leaf1 = Un[x_pm] @ Um')],
+    "leaf_reversed": [('Q = leaf1 + leaf2 + leaf3 + leaf4', 'Q = leaf1 + _dag(leaf2) + leaf3 + leaf4')],
+    "leaf_dropped": [('Q = leaf1 + leaf2 + leaf3 + leaf4', 'Q = leaf1 + leaf2 + leaf4')],
+    "leaf_wrong_site": [('@ Un[x_mn_pm] @', '@ Un[x_pm] @')],
+    "normalisation": [('(Q - _dag(Q)) / 8j', '(Q - _dag(Q)) / 4j')],
+    "not_antihermitian_part": [('(Q - _dag(Q)) / 8j', 'Q / 4j')],
+    "clover_sign": [('AD -= kappa * csw * term', 'AD += kappa * csw * term')],
+    "clover_half": [('AD -= kappa * csw * term', 'AD -= 0.5 * kappa * csw * term')],
+    "sigma_sign": [('return 0.5j * (g[mu]', 'return -0.5j * (g[mu]')],
+    "neighbour_step_two": [('cf[mu] = (coords[mu] + 1)', 'cf[mu] = (coords[mu] + 2)')],
+}
+
+
+@pytest.mark.parametrize("kind", sorted(OPERATOR_MUTATIONS))
+def test_operator_mutation_is_caught(kind):
+    ns = mutated_module(O, OPERATOR_MUTATIONS[kind])
+    errs = pins.all_operator_pins(ns["WilsonClover"])
+    assert max(errs.values()) > PIN_TOL, errs
+
+
+def test_unmutated_operator_passes_every_pin():
+    errs = pins.all_operator_pins(O.WilsonClover)
+    assert max(errs.values()) < 1e-13, errs
+
+
+# ---------------------------------------------------------------- solver mutations
+def solver_pin_error(ns):
+    """Dense-LU solve on 2^4 and the two-step Jacobi polynomial; the larger relative error."""
+    dims = (2, 2, 2, 2)
+    op = O.WilsonClover(I.random_links(dims, 0.3, 0), dims, 0.115, 1.0)
+    A = op.dense()
+    B = I.z4_noise(dims, 4, seed=1)
+    X_lu = np.linalg.solve(A, B.reshape(op.N, 4))
+    try:
+        r = ns["solve"](op, B, j=2, tol=1e-12, maxit=300, max_restarts=0)
+        e_solve = np.linalg.norm(r.X.reshape(op.N, 4) - X_lu) / np.linalg.norm(X_lu)
+    except Exception:
+        e_solve = np.inf
+    Dinv = np.linalg.inv(op.dense_site_diagonal())
+    u = I.gaussian_block(dims, 2, seed=5).reshape(op.N, 2)
+    want = Dinv @ u + (np.eye(op.N) - Dinv @ A) @ (Dinv @ u)
+    got = ns["jacobi"](op, u.reshape(op.lat.V, 4, 3, 2), 2).reshape(op.N, 2)
+    e_jac = np.linalg.norm(got - want) / np.linalg.norm(want)
+    e = max(e_solve, e_jac)
+    return e if np.isfinite(e) else np.inf
+
+
+SOLVER_MUTATIONS = {
+    "jacobi_sign": [('G = G + op.apply_site_diagonal', 'G = G - op.apply_site_diagonal')],
+    "jacobi_no_inverse": [('op.apply_site_diagonal(U - op.apply(G), inverse=True)',
+                           '(U - op.apply(G))')],
+    "gram_no_conj": [('A.reshape(-1, L).conj().T @ B', 'A.reshape(-1, L).T @ B')],
+    "gram_transposed": [('return A.reshape(-1, L).conj().T @ B.reshape(-1, L)',
+                         'return B.reshape(-1, L).conj().T @ A.reshape(-1, L)')],
+    "right_multiply_transposed": [('(X.reshape(-1, L) @ C)', '(X.reshape(-1, L) @ C.T)')],
+    "alpha_system_swapped": [('solve_small(herm_product(Rt, V), herm_product(Rt, R))',
+                              'solve_small(herm_product(Rt, R), herm_product(Rt, V))')],
+    "zeta_conjugated": [('zeta = np.vdot(W, R) / ww', 'zeta = np.vdot(R, W) / ww')],
+    "s_sign": [('S = P - zeta * V', 'S = P + zeta * V')],
+    "x_update_drops_zeta": [('X = X + zeta * F + G', 'X = X + F + G')],
+    "r_update_sign": [('R_new = R - zeta * W - Y', 'R_new = R - zeta * W + Y')],
+    "gamma_missing_zeta": [('herm_product(Rt, R_new) / zeta)', 'herm_product(Rt, R_new))')],
+    "p_update_uses_y": [('P = R_new + right_multiply(Uk, gamma)', 'P = R_new + right_multiply(Y, gamma)')],
+    "v_update_uses_u": [('V = W + right_multiply(Y, gamma)', 'V = W + right_multiply(Uk, gamma)')],
+    "w_not_refreshed": [('W = A(F)                                   # W_{k+1}',
+                         'W = W                                      # W_{k+1}')],
+}
+
+
+def invariant_error(ns):
+    dims = (2, 2, 2, 4)
+    op = O.WilsonClover(I.random_links(dims, 0.4, 2), dims, 0.12, 1.2)
+    B = I.z4_noise(dims, 3, seed=4)
+    try:
+        return pins.solver_invariant_error(ns["bbicggr"], op, B, j=2)
+    except Exception:
+        return np.inf
+
+
+@pytest.mark.parametrize("kind", sorted(SOLVER_MUTATIONS))
+def test_solver_mutation_is_caught(kind):
+    ns = mutated_module(S, SOLVER_MUTATIONS[kind])
+    assert max(solver_pin_error(ns), invariant_error(ns)) > PIN_TOL
+
+
+def test_unmutated_solver_passes_pins():
+    assert solver_pin_error(S.__dict__) < 1e-10
+    assert invariant_error(S.__dict__) < 1e-10
