@@ -1,0 +1,127 @@
+/*
+ * bbicggr.h -- C-ABI of the GB300 (sm_103a) preconditioned block BiCGGR solver for the
+ * O(a)-improved (clover) Wilson-Dirac equation with multiple right-hand sides.
+ *
+ * The problem is A X = B (Tadano, Kuramashi, Sakurai, arXiv:0907.3261, Sec. 2, Eq. (1)):
+ * A is the N x N clover Wilson-Dirac matrix on an Lx*Ly*Lz*Lt lattice, N = 12*V, V = Lx*Ly*Lz*Lt,
+ * and X, B are N x L blocks of L right-hand sides ("source vectors").
+ *
+ * Conventions (the paper leaves A's structure to its Ref. [blockbicggr_app]; these are the
+ * standard Sheikholeslami-Wohlert form in kappa normalisation, periodic boundaries):
+ *   (A psi)(x) = A_D(x) psi(x) - kappa sum_mu [(1 - g_mu) U_mu(x) psi(x+mu)
+ *                                             + (1 + g_mu) U_mu(x-mu)^H psi(x-mu)]
+ *   A_D(x) = 1 - kappa c_SW sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x), sigma = (i/2)[g_mu, g_nu],
+ *   F = (Q - Q^H)/(8i) with Q the four-leaf clover; chiral basis g_k = [[0,-i s_k],[i s_k,0]],
+ *   g_t = [[0,1],[1,0]], g_5 = diag(1,1,-1,-1).
+ *
+ * Layouts (all complex128, real and imaginary parts interleaved, 16-byte aligned):
+ *   site index        s = x + Lx*(y + Ly*(z + Lz*t))
+ *   links             [V][4 mu][3][3]: U_mu(x), the link from x to x+mu, row-major; mu = x,y,z,t
+ *   N x L blocks      [V][4 spin][3 colour][L]: element (row n, column i) at n*L + i, i.e. the
+ *                     paper's N x L matrix stored row-major, right-hand sides innermost.
+ *
+ * Pointers: every buffer argument may be device memory or host memory (pageable or pinned); the
+ * library finds out with cudaPointerGetAttributes.  Host buffers are staged through device
+ * buffers owned by the context, with cudaMemcpyAsync on the given stream, and a call that was given
+ * a host buffer synchronises the stream before it returns.  Device buffers must be 16-byte aligned.
+ * Ownership: the caller owns every buffer it passes; the library never frees or keeps a pointer to
+ * one after the call returns.  wd_create copies the links and derives the clover term into
+ * context-owned device memory; solver workspace is allocated at the first call with a given L and
+ * kept in the context until wd_destroy.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All device work of a call is
+ * ordered on it.  A context must not be used from two host threads at once.
+ * Errors: every entry point returns an int status (WD_OK = 0) and never aborts; wd_strerror gives
+ * the code's name and wd_last_error() a one-line description of the last failure in this thread.
+ */
+#ifndef BBICGGR_H
+#define BBICGGR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  WD_OK = 0,
+  WD_EINVAL = 1,          /* bad argument: dims < 2 or too large, L outside [1, WD_LMAX], j < 0,
+                             tol <= 0, NULL or misaligned pointer, a column of B that is zero */
+  WD_ENOMEM = 2,          /* device or pinned-host allocation failed */
+  WD_ECUDA = 3,           /* a CUDA runtime call failed; wd_last_error() has the CUDA message */
+  WD_NOT_CONVERGED = 4,   /* maxit reached, or true residual above tol after max_restarts */
+  WD_DIVERGED = 5,        /* max_i ||r_i|| / ||b_i|| exceeded opts.div_thresh (Sec. 3.3: 1e2) */
+  WD_BREAKDOWN = 6        /* singular L x L system (rank loss, Sec. 4), Tr[W^H W] = 0, a
+                             non-finite residual, or a singular clover block at wd_create */
+};
+
+#define WD_LMAX 16        /* largest number of right-hand sides per solve */
+
+typedef struct wd_ctx wd_ctx;   /* opaque; owned by the library */
+
+/* Solver options.  Fill with bbicggr_default_opts() and change what you need. */
+typedef struct {
+  int maxit;              /* outer iterations, default 10000 (summed over restarts) */
+  double div_thresh;      /* DIVERGED above this max relative recursive residual; default 1e2 */
+  int max_restarts;       /* restarts from X when the true residual is above tol; default 3 */
+  int precision;          /* 0: FP64 preconditioner (default); 1: FP32 preconditioner with FP32
+                             accumulation -- the outer recurrences, the products W = AF and
+                             Y = AG, the Gram matrices, the L x L solves and the true residual stay
+                             FP64 */
+  double* history;        /* optional host array: max_i ||r_i||/||b_i|| after every R update */
+  int history_len;        /* capacity of history (entries beyond it are dropped) */
+} bbicggr_opts;
+
+/* Solve report.  rec_resid and true_resid, when not NULL, are caller-owned host arrays of L. */
+typedef struct {
+  int status;             /* same as the return value */
+  int iters;              /* outer iterations k (summed over restarts) */
+  int restarts;           /* restarts taken */
+  long long mvm_paper;    /* #MVM as the paper counts it: L * sum over runs of 2(j+1)k + 1 */
+  long long mvm_actual;   /* column-MVMs with a hopping term actually applied (the first Jacobi
+                             sweep from G = 0 is site-local and not counted) */
+  double max_rec_resid;   /* max_i ||r_i|| / ||b_i|| of the recursive residual at exit */
+  double max_true_resid;  /* max_i ||b_i - A x_i|| / ||b_i|| at exit */
+  double* rec_resid;      /* [L] or NULL */
+  double* true_resid;     /* [L] or NULL */
+  int history_count;      /* entries written to opts->history */
+  double seconds;         /* wall time of the call (host clock, includes host<->device copies) */
+} bbicggr_info;
+
+/* Build the operator A for the given links (Sec. 2; kappa and c_SW as in Sec. 3.1).
+ * links: [V][4][3][3] complex128 (host or device); dims: {Lx, Ly, Lz, Lt}, each >= 2, V <= 2^26.
+ * Copies the links, builds F_{mu nu} from the four-leaf clover, the two 6x6 chiral blocks of A_D per
+ * site and their inverses (FP64), all in context-owned device memory.  *out is NULL on failure.
+ * Returns WD_BREAKDOWN if some clover block is singular. */
+int wd_create(wd_ctx** out, const void* links, const int dims[4], double kappa, double csw,
+              void* stream);
+
+/* Release everything the context owns.  NULL is a no-op. */
+void wd_destroy(wd_ctx* ctx);
+
+/* Y = A X for an N x L block (Sec. 2, Eq. (1)).  X and Y must not overlap.  1 <= L <= WD_LMAX. */
+int wd_apply(wd_ctx* ctx, const void* X, void* Y, int L, void* stream);
+
+/* G = M R, the j-step Jacobi preconditioner of Sec. 2 from the zero initial guess (Sec. 3.3):
+ * G = sum_{i<j} (I - A_D^{-1} A)^i A_D^{-1} R for j >= 1 and G = R for j = 0.  Computed as j sweeps
+ * G <- A_D^{-1}(R + kappa H G), H the hopping term.  `precision` as in bbicggr_opts (0 = FP64,
+ * 1 = FP32 sweeps).  R and G must not overlap. */
+int jacobi_precond(wd_ctx* ctx, const void* R, void* G, int L, int j, int precision, void* stream);
+
+/* Preconditioned block BiCGGR (Sec. 2, algorithm box) with the j-step Jacobi preconditioner,
+ * R~_0 = R_0 (Sec. 3.3).  X holds X_0 on entry (zero it for the paper's X_0 = 0) and the solution
+ * on exit.  Iterates until max_i ||r_i||/||b_i|| <= tol on the recursive residual, checked after
+ * every R update; then recomputes the true residual and restarts from X while it is above tol
+ * (at most opts->max_restarts times).  On a non-OK return X holds the last iterate and info is
+ * filled.  opts may be NULL (defaults); info may be NULL.  Every column of B must be non-zero. */
+int bbicggr_solve(wd_ctx* ctx, const void* B, void* X, int L, int j, double tol,
+                  const bbicggr_opts* opts, bbicggr_info* info, void* stream);
+
+void bbicggr_default_opts(bbicggr_opts* opts);
+const char* wd_strerror(int code);
+const char* wd_last_error(void);
+
+/* Lattice size and parameters of a context (for bindings): dims[4], V, kappa, c_SW. */
+int wd_query(const wd_ctx* ctx, int dims[4], long long* volume, double* kappa, double* csw);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BBICGGR_H */

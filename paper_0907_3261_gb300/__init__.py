@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) preconditioned block BiCGGR for the clover Wilson-Dirac equation (arXiv:0907.3261).
+
+The compute path is the CUDA library ``libbbicggr.so`` (sources in ``csrc/``, C-ABI in
+``include/bbicggr.h``); ``_lib`` is its ctypes binding with the same entry-point names.
+``inputs`` holds the seeded synthetic input generators.
+"""
+from ._lib import (WD_BREAKDOWN, WD_DIVERGED, WD_LMAX, WD_NOT_CONVERGED, WD_OK, Context, WDError,
+                   bbicggr_solve, jacobi_precond, wd_apply, wd_create, wd_destroy)
+
+__all__ = ["wd_create", "wd_destroy", "wd_apply", "jacobi_precond", "bbicggr_solve", "Context",
+           "WDError", "WD_OK", "WD_NOT_CONVERGED", "WD_DIVERGED", "WD_BREAKDOWN", "WD_LMAX"]

@@ -1,0 +1,232 @@
+"""ctypes binding of the C-ABI in include/bbicggr.h: the same entry points, argument marshalling only.
+
+Every computation runs in libbbicggr.so; this module converts torch tensors (device buffers) and
+numpy arrays (host buffers) into pointers and sizes, passes the CUDA stream, and turns return
+codes into exceptions.  Block vectors are complex128 arrays of shape (V, 4, 3, L) or (12*V, L).
+If the library has not been built the first call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libbbicggr.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "bbicggr.h")
+
+WD_OK, WD_EINVAL, WD_ENOMEM, WD_ECUDA = 0, 1, 2, 3
+WD_NOT_CONVERGED, WD_DIVERGED, WD_BREAKDOWN = 4, 5, 6
+SOLVER_STATUSES = (WD_OK, WD_NOT_CONVERGED, WD_DIVERGED, WD_BREAKDOWN)
+WD_LMAX = 16
+
+
+class WDError(RuntimeError):
+    def __init__(self, code: int, name: str, message: str):
+        super().__init__(f"{name}: {message}")
+        self.code = code
+
+
+class Opts(C.Structure):
+    _fields_ = [("maxit", C.c_int), ("div_thresh", C.c_double), ("max_restarts", C.c_int),
+                ("precision", C.c_int), ("history", C.POINTER(C.c_double)),
+                ("history_len", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("restarts", C.c_int),
+                ("mvm_paper", C.c_longlong), ("mvm_actual", C.c_longlong),
+                ("max_rec_resid", C.c_double), ("max_true_resid", C.c_double),
+                ("rec_resid", C.POINTER(C.c_double)), ("true_resid", C.POINTER(C.c_double)),
+                ("history_count", C.c_int), ("seconds", C.c_double)]
+
+
+_lib = None
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/bbicggr.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    """Load libbbicggr.so (raises if it is missing: build it with paper_0907_3261_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: the CUDA library must be built "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = C.CDLL(LIB_PATH)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    L.wd_create.argtypes = [C.POINTER(vp), vp, C.POINTER(C.c_int), d, d, vp]
+    L.wd_destroy.argtypes = [vp]
+    L.wd_destroy.restype = None
+    L.wd_apply.argtypes = [vp, vp, vp, i, vp]
+    L.jacobi_precond.argtypes = [vp, vp, vp, i, i, i, vp]
+    L.bbicggr_solve.argtypes = [vp, vp, vp, i, i, d, C.POINTER(Opts), C.POINTER(Info), vp]
+    L.bbicggr_default_opts.argtypes = [C.POINTER(Opts)]
+    L.bbicggr_default_opts.restype = None
+    L.wd_strerror.argtypes = [i]
+    L.wd_strerror.restype = C.c_char_p
+    L.wd_last_error.argtypes = []
+    L.wd_last_error.restype = C.c_char_p
+    L.wd_query.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(d),
+                           C.POINTER(d)]
+    for name in ("wd_create", "wd_apply", "jacobi_precond", "bbicggr_solve", "wd_query"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _raise(code: int):
+    L = lib()
+    raise WDError(code, L.wd_strerror(code).decode(), L.wd_last_error().decode())
+
+
+def _check(code: int):
+    if code != WD_OK:
+        _raise(code)
+
+
+# ---------------------------------------------------------------- buffer marshalling
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr_and_L(x, what: str):
+    """(pointer, L, keepalive) for a complex128 block vector on the device (torch) or host (numpy)."""
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.complex128:
+            raise TypeError(f"{what} must be complex128")
+        if not x.is_contiguous():
+            raise ValueError(f"{what} must be contiguous")
+        return C.c_void_p(x.data_ptr()), int(x.shape[-1]), x
+    a = np.ascontiguousarray(x, dtype=np.complex128) if not isinstance(x, np.ndarray) else x
+    if a.dtype != np.complex128 or not a.flags.c_contiguous:
+        raise TypeError(f"{what} must be a C-contiguous complex128 array")
+    return C.c_void_p(a.ctypes.data), int(a.shape[-1]), a
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _empty_like(x):
+    if _is_torch(x):
+        import torch
+        return torch.empty_like(x)
+    return np.empty_like(x)
+
+
+class Context:
+    """Owns a wd_ctx*; freed by wd_destroy (or when garbage collected)."""
+
+    def __init__(self, handle: int, dims, kappa: float, csw: float):
+        self.handle = C.c_void_p(handle)
+        self.dims = tuple(dims)
+        self.kappa = kappa
+        self.csw = csw
+        self.V = int(np.prod(dims))
+
+    def close(self):
+        if self.handle and self.handle.value:
+            lib().wd_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- entry points
+def wd_create(links, dims, kappa: float, csw: float, stream=None) -> Context:
+    """Build A for ``links`` ([V][4][3][3] complex128, host numpy or device torch)."""
+    p, _, keep = _ptr_and_L(links, "links")
+    out = C.c_void_p()
+    d = (C.c_int * 4)(*[int(v) for v in dims])
+    _check(lib().wd_create(C.byref(out), p, d, float(kappa), float(csw), _stream(stream)))
+    del keep
+    return Context(out.value, dims, kappa, csw)
+
+
+def wd_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def wd_apply(ctx: Context, X, Y=None, stream=None):
+    """Y = A X."""
+    px, L, kx = _ptr_and_L(X, "X")
+    if Y is None:
+        Y = _empty_like(X)
+    py, _, ky = _ptr_and_L(Y, "Y")
+    _check(lib().wd_apply(ctx.handle, px, py, L, _stream(stream)))
+    return Y
+
+
+def jacobi_precond(ctx: Context, R, j: int, G=None, precision: int = 0, stream=None):
+    """G = M R, j Jacobi sweeps from G = 0 (precision 0 = FP64, 1 = FP32 sweeps)."""
+    pr, L, kr = _ptr_and_L(R, "R")
+    if G is None:
+        G = _empty_like(R)
+    pg, _, kg = _ptr_and_L(G, "G")
+    _check(lib().jacobi_precond(ctx.handle, pr, pg, L, int(j), int(precision), _stream(stream)))
+    return G
+
+
+def bbicggr_solve(ctx: Context, B, X=None, j: int = 12, tol: float = 1e-12, maxit: int = 10000,
+                  div_thresh: float = 1e2, max_restarts: int = 3, precision: int = 0,
+                  history: int = 0, stream=None):
+    """Solve A X = B by preconditioned block BiCGGR.  Returns (X, info dict).
+
+    ``X`` (if given) holds X_0 and receives the solution; by default X_0 = 0.  Solver outcomes
+    (WD_NOT_CONVERGED, WD_DIVERGED, WD_BREAKDOWN) are reported in ``info["status"]``; argument and
+    CUDA errors raise WDError."""
+    pb, L, kb = _ptr_and_L(B, "B")
+    if X is None:
+        if _is_torch(B):
+            import torch
+            X = torch.zeros_like(B)
+        else:
+            X = np.zeros_like(B)
+    px, _, kx = _ptr_and_L(X, "X")
+    o = Opts()
+    lib().bbicggr_default_opts(C.byref(o))
+    o.maxit, o.div_thresh, o.max_restarts, o.precision = int(maxit), float(div_thresh), \
+        int(max_restarts), int(precision)
+    hist = (C.c_double * max(history, 1))()
+    if history:
+        o.history = C.cast(hist, C.POINTER(C.c_double))
+        o.history_len = int(history)
+    rec = (C.c_double * L)()
+    tru = (C.c_double * L)()
+    info = Info()
+    info.rec_resid = C.cast(rec, C.POINTER(C.c_double))
+    info.true_resid = C.cast(tru, C.POINTER(C.c_double))
+    rc = lib().bbicggr_solve(ctx.handle, pb, px, L, int(j), float(tol), C.byref(o),
+                             C.byref(info), _stream(stream))
+    if rc not in SOLVER_STATUSES:
+        _raise(rc)
+    out = dict(status=rc, status_name=lib().wd_strerror(rc).decode(), iters=info.iters,
+               restarts=info.restarts, mvm_paper=info.mvm_paper, mvm_actual=info.mvm_actual,
+               max_rec_resid=info.max_rec_resid, max_true_resid=info.max_true_resid,
+               rec_resid=np.array(rec[:]), true_resid=np.array(tru[:]),
+               history=np.array(hist[:info.history_count]), seconds=info.seconds)
+    return X, out

@@ -1,0 +1,541 @@
+// C-ABI of the library (declared in include/bbicggr.h): context creation, Y = A X, the Jacobi
+// preconditioner, and the preconditioned block BiCGGR driver of arXiv:0907.3261, Sec. 2.
+//
+// The driver keeps every L x L quantity on the device (SolverState) and launches the iteration as
+// a fixed sequence of kernels on the caller's stream.  The host reads back L residual norms and a
+// status word once per outer iteration, right after the R update, where the stopping test of the
+// algorithm box sits; a singular L x L system makes the later kernels of the iteration leave X and
+// R untouched, so the returned iterate is the last consistent one.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/bbicggr.h"
+#include "internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+#define CU(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? WD_ENOMEM : WD_ECUDA;                  \
+    }                                                                                 \
+  } while (0)
+
+#define CHECK(rc)              \
+  do {                         \
+    int rc_ = (rc);            \
+    if (rc_ != WD_OK) return rc_; \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t need) {
+    if (bytes >= need) return WD_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    CU(cudaMalloc(&p, need));
+    bytes = need;
+    return WD_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  double* d() const { return static_cast<double*>(p); }
+};
+
+// Host mirror of what the driver reads back each iteration.
+struct HostMirror {
+  double rnorm2[WD_LMAX];
+  int status;
+};
+
+}  // namespace
+
+struct wd_ctx {
+  Op op{};
+  int device = 0;
+  // solver workspace for the current L
+  int L = 0;
+  DevBuf blk[13];          // X R P V W F U G Y Rt T B Xs
+  DevBuf part;             // reduction partials
+  SolverState* st = nullptr;
+  HostMirror* hm = nullptr;
+  double* bnorm2_dev = nullptr;
+  // staging for host pointers in wd_apply / jacobi_precond
+  DevBuf stage_in, stage_out;
+};
+
+namespace {
+
+enum { B_X, B_R, B_P, B_V, B_W, B_F, B_U, B_G, B_Y, B_RT, B_T, B_B, B_XS, B_COUNT };
+
+size_t block_bytes(const wd_ctx* c, int L) { return (size_t)c->op.g.V * 12 * L * 16; }
+
+int check_L(int L) {
+  if (L < 1 || L > WD_LMAX) {
+    set_err("L = %d outside [1, %d]", L, WD_LMAX);
+    return WD_EINVAL;
+  }
+  return WD_OK;
+}
+
+int check_ptr(const void* p, const char* name) {
+  if (!p) {
+    set_err("%s is NULL", name);
+    return WD_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0 && is_device_ptr(p)) {
+    set_err("%s is not 16-byte aligned", name);
+    return WD_EINVAL;
+  }
+  return WD_OK;
+}
+
+int ensure_workspace(wd_ctx* c, int L) {
+  if (c->L == L && c->st) return WD_OK;
+  for (auto& b : c->blk) b.release();
+  c->L = 0;
+  const size_t bytes = block_bytes(c, L);
+  for (int i = 0; i < B_COUNT; ++i) CHECK(c->blk[i].ensure(bytes));
+  CHECK(c->part.ensure((size_t)152 * 4 * PART_STRIDE * sizeof(double2)));
+  if (!c->st) CU(cudaMalloc(&c->st, sizeof(SolverState)));
+  if (!c->bnorm2_dev) CU(cudaMalloc(&c->bnorm2_dev, 2 * WD_LMAX * sizeof(double)));
+  if (!c->hm) CU(cudaMallocHost(&c->hm, sizeof(HostMirror)));
+  c->L = L;
+  return WD_OK;
+}
+
+// Device pointer for an input that may live on the host: copies into `stage` when needed.
+int stage_input(const void* p, size_t bytes, DevBuf& stage, const double** out, bool* staged,
+                cudaStream_t s) {
+  if (is_device_ptr(p)) {
+    *out = static_cast<const double*>(p);
+    *staged = false;
+    return WD_OK;
+  }
+  CHECK(stage.ensure(bytes));
+  CU(cudaMemcpyAsync(stage.p, p, bytes, cudaMemcpyHostToDevice, s));
+  *out = stage.d();
+  *staged = true;
+  return WD_OK;
+}
+
+// G = M R with j Jacobi sweeps; `a` and `b` are two scratch blocks, the result pointer is
+// returned in *res (one of a, b).  j = 0 copies R.
+int precondition(wd_ctx* c, const double* R, double* a, double* b, double** res, int L, int j,
+                 long long* hop_count, cudaStream_t s) {
+  const Op& op = c->op;
+  if (j == 0) {
+    CU(cudaMemcpyAsync(a, R, block_bytes(c, L), cudaMemcpyDeviceToDevice, s));
+    *res = a;
+    return WD_OK;
+  }
+  CU(launch_site_inverse_f64(op, R, a, L, s));
+  double* cur = a;
+  double* nxt = b;
+  for (int i = 1; i < j; ++i) {
+    CU(launch_jacobi_f64(op, cur, R, nxt, L, s));
+    if (hop_count) ++*hop_count;
+    double* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  *res = cur;
+  return WD_OK;
+}
+
+int read_back(wd_ctx* c, cudaStream_t s) {
+  CU(cudaMemcpyAsync(c->hm, reinterpret_cast<char*>(c->st) + offsetof(SolverState, rnorm2),
+                     sizeof(double) * WD_LMAX, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(&c->hm->status, reinterpret_cast<char*>(c->st) + offsetof(SolverState, status),
+                     sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return WD_OK;
+}
+
+struct RunResult {
+  int status;
+  int k;
+  double rec[WD_LMAX];
+};
+
+double max_rel(const double* n2, const double* b2, int L, double* rel) {
+  double m = 0.0;
+  for (int i = 0; i < L; ++i) {
+    const double r = std::sqrt(n2[i]) / std::sqrt(b2[i]);
+    if (rel) rel[i] = r;
+    if (!(r <= m)) m = r;   // NaN propagates
+  }
+  return m;
+}
+
+// One run of preconditioned block BiCGGR from the current X (Sec. 2, algorithm box).
+int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, double tol, int maxit,
+                double div_thresh, const double* b2, bbicggr_opts* o, int* hist_n,
+                long long* hop_count, RunResult* out, cudaStream_t s) {
+  const Op& op = c->op;
+  const long long rows = (long long)op.g.V * 12;
+  const size_t bytes = block_bytes(c, L);
+  double* R = c->blk[B_R].d();
+  double* P = c->blk[B_P].d();
+  double* V = c->blk[B_V].d();
+  double* W = c->blk[B_W].d();
+  double* U = c->blk[B_U].d();
+  double* Y = c->blk[B_Y].d();
+  double* Rt = c->blk[B_RT].d();
+  double* pF = c->blk[B_F].d();
+  double* pG = c->blk[B_G].d();
+  double* pT = c->blk[B_T].d();
+  double2* part = static_cast<double2*>(c->part.p);
+  SolverState* st = c->st;
+  CU(cudaMemsetAsync(&st->status, 0, sizeof(int), s));
+
+  // R_0 = B - A X_0;  P_0 = R_0;  R~_0 = R_0
+  CU(launch_resid_f64(op, X, B, R, L, s));
+  ++*hop_count;
+  CU(cudaMemcpyAsync(P, R, bytes, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync(Rt, R, bytes, cudaMemcpyDeviceToDevice, s));
+  CU(launch_gram(Rt, R, L, rows, part, st, GRAM_RTR, true, s));
+  CHECK(read_back(c, s));
+  double m = max_rel(c->hm->rnorm2, b2, L, out->rec);
+  out->k = 0;
+  if (o->history && *hist_n < o->history_len) o->history[(*hist_n)++] = m;
+  if (m <= tol) { out->status = WD_OK; return WD_OK; }
+  if (!std::isfinite(m)) { out->status = WD_BREAKDOWN; return WD_OK; }
+
+  // F_0 = M R_0;  V_0 = W_0 = A F_0
+  double* res;
+  CHECK(precondition(c, R, pF, pT, &res, L, j, hop_count, s));
+  if (res != pF) { pT = pF; pF = res; }
+  CU(launch_apply_f64(op, pF, W, L, s));
+  ++*hop_count;
+  CU(cudaMemcpyAsync(V, W, bytes, cudaMemcpyDeviceToDevice, s));
+  CU(launch_traces(W, R, L, rows, part, st, s));
+  CU(launch_gram(Rt, V, L, rows, part, st, GRAM_RTV, false, s));
+
+  int k = 0;
+  for (;;) {
+    if (k >= maxit) { out->status = WD_NOT_CONVERGED; break; }
+    CU(launch_solve_alpha(st, L, s));                       // alpha_k, zeta_k
+    CU(launch_update_u(P, V, U, L, rows, st, s));           // U_k = (P_k - zeta_k V_k) alpha_k
+    CHECK(precondition(c, U, pG, pT, &res, L, j, hop_count, s));   // G_k = M U_k
+    if (res != pG) { pT = pG; pG = res; }
+    CU(launch_apply_f64(op, pG, Y, L, s));                  // Y_k = A G_k
+    ++*hop_count;
+    CU(launch_update_xr(X, pF, pG, R, W, Y, Rt, L, rows, part, st, s));   // X_{k+1}, R_{k+1}
+    CHECK(read_back(c, s));
+    if (c->hm->status != ST_OK) { out->status = WD_BREAKDOWN; break; }
+    ++k;
+    m = max_rel(c->hm->rnorm2, b2, L, out->rec);
+    if (o->history && *hist_n < o->history_len) o->history[(*hist_n)++] = m;
+    if (!std::isfinite(m)) { out->status = WD_BREAKDOWN; break; }
+    if (m <= tol) { out->status = WD_OK; break; }
+    if (m > div_thresh) { out->status = WD_DIVERGED; break; }
+    CHECK(precondition(c, R, pF, pT, &res, L, j, hop_count, s));   // F_{k+1} = M R_{k+1}
+    if (res != pF) { pT = pF; pF = res; }
+    CU(launch_apply_f64(op, pF, W, L, s));                  // W_{k+1} = A F_{k+1}
+    ++*hop_count;
+    CU(launch_traces(W, R, L, rows, part, st, s));          // Tr[W^H R], Tr[W^H W]
+    CU(launch_solve_gamma(st, L, s));                       // gamma_k
+    CU(launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s));   // P_{k+1}, V_{k+1}
+  }
+  out->k = k;
+  return WD_OK;
+}
+
+// FP32 copies of links and clover inverse for the FP32 preconditioner.
+__global__ void to_float_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+void bbicggr_default_opts(bbicggr_opts* o) {
+  if (!o) return;
+  o->maxit = 10000;
+  o->div_thresh = 1e2;
+  o->max_restarts = 3;
+  o->precision = 0;
+  o->history = nullptr;
+  o->history_len = 0;
+}
+
+const char* wd_strerror(int code) {
+  switch (code) {
+    case WD_OK: return "WD_OK";
+    case WD_EINVAL: return "WD_EINVAL";
+    case WD_ENOMEM: return "WD_ENOMEM";
+    case WD_ECUDA: return "WD_ECUDA";
+    case WD_NOT_CONVERGED: return "WD_NOT_CONVERGED";
+    case WD_DIVERGED: return "WD_DIVERGED";
+    case WD_BREAKDOWN: return "WD_BREAKDOWN";
+    default: return "WD_UNKNOWN";
+  }
+}
+
+const char* wd_last_error(void) { return g_err; }
+
+void wd_destroy(wd_ctx* c) {
+  if (!c) return;
+  cudaFree(c->op.links);
+  cudaFree(c->op.clov);
+  cudaFree(c->op.clov_inv);
+  cudaFree(c->op.links32);
+  cudaFree(c->op.clov_inv32);
+  for (auto& b : c->blk) b.release();
+  c->part.release();
+  c->stage_in.release();
+  c->stage_out.release();
+  cudaFree(c->st);
+  cudaFree(c->bnorm2_dev);
+  cudaFreeHost(c->hm);
+  delete c;
+}
+
+static int create_impl(wd_ctx* c, const void* links, const int dims[4], cudaStream_t s) {
+  Op& op = c->op;
+  const size_t V = op.g.V;
+  const size_t lbytes = V * 4 * 18 * sizeof(double);
+  CU(cudaMalloc(&op.links, lbytes));
+  CU(cudaMalloc(&op.clov, V * 2 * CLOV_REALS * sizeof(double)));
+  CU(cudaMalloc(&op.clov_inv, V * 2 * CLOV_REALS * sizeof(double)));
+  CU(cudaMalloc(&op.links32, V * 4 * 18 * sizeof(float)));
+  CU(cudaMalloc(&op.clov_inv32, V * 2 * CLOV_REALS * sizeof(float)));
+  CU(cudaMemcpyAsync(op.links, links, lbytes, cudaMemcpyDefault, s));
+  int* flag;
+  CU(cudaMalloc(&flag, sizeof(int)));
+  CU(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  CU(launch_clover_build(op, flag, s));
+  const size_t n = V * 4 * 18;
+  to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(op.links, op.links32, n);
+  CU(cudaGetLastError());
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(flag);
+  CU(e);
+  if (h) {
+    set_err("a 6x6 clover block A_D is singular for kappa=%g c_SW=%g", op.kappa, op.csw);
+    return WD_BREAKDOWN;
+  }
+  return WD_OK;
+}
+
+int wd_create(wd_ctx** out, const void* links, const int dims[4], double kappa, double csw,
+              void* stream) {
+  if (!out) { set_err("out is NULL"); return WD_EINVAL; }
+  *out = nullptr;
+  if (!links || !dims) { set_err("links or dims is NULL"); return WD_EINVAL; }
+  long long V = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (dims[m] < 2 || dims[m] > 4096) {
+      set_err("dims[%d] = %d outside [2, 4096]", m, dims[m]);
+      return WD_EINVAL;
+    }
+    V *= dims[m];
+  }
+  if (V > (1LL << 26)) { set_err("volume %lld above 2^26 sites", V); return WD_EINVAL; }
+  if (!std::isfinite(kappa) || !std::isfinite(csw)) { set_err("kappa or c_SW not finite"); return WD_EINVAL; }
+  if (reinterpret_cast<uintptr_t>(links) % 16 != 0 && is_device_ptr(links)) {
+    set_err("links not 16-byte aligned");
+    return WD_EINVAL;
+  }
+  wd_ctx* c = new (std::nothrow) wd_ctx();
+  if (!c) { set_err("host allocation failed"); return WD_ENOMEM; }
+  cudaGetDevice(&c->device);
+  c->op.g = make_geom(dims);
+  c->op.kappa = kappa;
+  c->op.csw = csw;
+  int rc = create_impl(c, links, dims, static_cast<cudaStream_t>(stream));
+  if (rc != WD_OK) { wd_destroy(c); return rc; }
+  *out = c;
+  return WD_OK;
+}
+
+int wd_query(const wd_ctx* c, int dims[4], long long* volume, double* kappa, double* csw) {
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  if (dims) for (int m = 0; m < 4; ++m) dims[m] = c->op.g.d[m];
+  if (volume) *volume = c->op.g.V;
+  if (kappa) *kappa = c->op.kappa;
+  if (csw) *csw = c->op.csw;
+  return WD_OK;
+}
+
+int wd_apply(wd_ctx* c, const void* X, void* Y, int L, void* stream) {
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  CHECK(check_L(L));
+  CHECK(check_ptr(X, "X"));
+  CHECK(check_ptr(Y, "Y"));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = block_bytes(c, L);
+  const double* xd;
+  bool staged_x;
+  CHECK(stage_input(X, bytes, c->stage_in, &xd, &staged_x, s));
+  const bool y_dev = is_device_ptr(Y);
+  double* yd = static_cast<double*>(Y);
+  if (!y_dev) { CHECK(c->stage_out.ensure(bytes)); yd = c->stage_out.d(); }
+  CU(launch_apply_f64(c->op, xd, yd, L, s));
+  if (!y_dev) CU(cudaMemcpyAsync(Y, yd, bytes, cudaMemcpyDeviceToHost, s));
+  if (staged_x || !y_dev) CU(cudaStreamSynchronize(s));
+  return WD_OK;
+}
+
+int jacobi_precond(wd_ctx* c, const void* R, void* G, int L, int j, int precision, void* stream) {
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  CHECK(check_L(L));
+  CHECK(check_ptr(R, "R"));
+  CHECK(check_ptr(G, "G"));
+  if (j < 0) { set_err("j = %d < 0", j); return WD_EINVAL; }
+  if (precision != 0) { set_err("precision %d not available", precision); return WD_EINVAL; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = block_bytes(c, L);
+  const double* rd;
+  bool staged_r;
+  CHECK(stage_input(R, bytes, c->stage_in, &rd, &staged_r, s));
+  const bool g_dev = is_device_ptr(G);
+  double* gd = static_cast<double*>(G);
+  if (!g_dev) { CHECK(c->stage_out.ensure(bytes)); gd = c->stage_out.d(); }
+  // ping-pong between the output and one workspace block
+  CHECK(ensure_workspace(c, L));
+  double* tmp = c->blk[B_T].d();
+  double* res;
+  // Arrange the sweeps so that the last one lands in gd: with j sweeps the result sits in the
+  // first buffer when j is odd.
+  double* first = (j % 2 == 1) ? gd : tmp;
+  double* second = (j % 2 == 1) ? tmp : gd;
+  CHECK(precondition(c, rd, first, second, &res, L, j, nullptr, s));
+  if (res != gd) CU(cudaMemcpyAsync(gd, res, bytes, cudaMemcpyDeviceToDevice, s));
+  if (!g_dev) CU(cudaMemcpyAsync(G, gd, bytes, cudaMemcpyDeviceToHost, s));
+  if (staged_r || !g_dev) CU(cudaStreamSynchronize(s));
+  return WD_OK;
+}
+
+int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
+                  const bbicggr_opts* opts, bbicggr_info* info, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  CHECK(check_L(L));
+  CHECK(check_ptr(B, "B"));
+  CHECK(check_ptr(X, "X"));
+  if (j < 0) { set_err("j = %d < 0", j); return WD_EINVAL; }
+  if (!(tol > 0.0)) { set_err("tol must be > 0"); return WD_EINVAL; }
+  bbicggr_opts o;
+  bbicggr_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.maxit < 0 || o.max_restarts < 0 || !(o.div_thresh > 0.0)) {
+    set_err("invalid options");
+    return WD_EINVAL;
+  }
+  if (o.precision != 0) { set_err("precision %d not available", o.precision); return WD_EINVAL; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CHECK(ensure_workspace(c, L));
+  const size_t bytes = block_bytes(c, L);
+  const long long rows = (long long)c->op.g.V * 12;
+
+  const double* Bd = static_cast<const double*>(B);
+  if (!is_device_ptr(B)) {
+    CU(cudaMemcpyAsync(c->blk[B_B].d(), B, bytes, cudaMemcpyHostToDevice, s));
+    Bd = c->blk[B_B].d();
+  }
+  const bool x_dev = is_device_ptr(X);
+  double* Xd = static_cast<double*>(X);
+  if (!x_dev) {
+    Xd = c->blk[B_XS].d();
+    CU(cudaMemcpyAsync(Xd, X, bytes, cudaMemcpyHostToDevice, s));
+  }
+  double b2[WD_LMAX];
+  CU(launch_colnorms(Bd, L, rows, static_cast<double2*>(c->part.p), c->bnorm2_dev, s));
+  CU(cudaMemcpyAsync(b2, c->bnorm2_dev, L * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  for (int i = 0; i < L; ++i)
+    if (!(b2[i] > 0.0) || !std::isfinite(b2[i])) {
+      set_err("column %d of B is zero or not finite", i);
+      return WD_EINVAL;
+    }
+
+  int status = WD_OK, iters = 0, restarts = 0, hist_n = 0;
+  long long mvm_paper = 0, hops = 0;
+  RunResult rr{};
+  double true_rel[WD_LMAX];
+  double mtrue = 0.0;
+  for (;;) {
+    long long hop_run = 0;
+    CHECK(run_bbicggr(c, Bd, Xd, L, j, tol, o.maxit - iters, o.div_thresh, b2, &o, &hist_n,
+                      &hop_run, &rr, s));
+    iters += rr.k;
+    hops += hop_run;
+    mvm_paper += (long long)L * (2LL * (j + 1) * rr.k + 1);
+    // true residual ||b_i - A x_i|| / ||b_i||
+    double* T = c->blk[B_T].d();
+    CU(launch_resid_f64(c->op, Xd, Bd, T, L, s));
+    ++hops;
+    double t2[WD_LMAX];
+    CU(launch_colnorms(T, L, rows, static_cast<double2*>(c->part.p), c->bnorm2_dev + WD_LMAX, s));
+    CU(cudaMemcpyAsync(t2, c->bnorm2_dev + WD_LMAX, L * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    mtrue = max_rel(t2, b2, L, true_rel);
+    status = rr.status;
+    if (status != WD_OK) break;
+    if (mtrue <= tol) break;
+    if (restarts >= o.max_restarts || iters >= o.maxit) { status = WD_NOT_CONVERGED; break; }
+    ++restarts;
+  }
+  if (!x_dev) {
+    CU(cudaMemcpyAsync(X, Xd, bytes, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+  }
+  if (info) {
+    info->status = status;
+    info->iters = iters;
+    info->restarts = restarts;
+    info->mvm_paper = mvm_paper;
+    info->mvm_actual = hops * L;
+    double mr = 0.0;
+    for (int i = 0; i < L; ++i) mr = (rr.rec[i] > mr || std::isnan(rr.rec[i])) ? rr.rec[i] : mr;
+    info->max_rec_resid = mr;
+    info->max_true_resid = mtrue;
+    if (info->rec_resid) std::memcpy(info->rec_resid, rr.rec, L * sizeof(double));
+    if (info->true_resid) std::memcpy(info->true_resid, true_rel, L * sizeof(double));
+    info->history_count = hist_n;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (status != WD_OK)
+    set_err("bbicggr_solve: %s after %d iterations (max recursive residual %.3e, true %.3e)",
+            wd_strerror(status), iters, info ? info->max_rec_resid : 0.0, mtrue);
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,446 @@
+// Tall-skinny block operations of preconditioned block BiCGGR (arXiv:0907.3261, Sec. 2, the
+// algorithm box): the L x L Gram products R~_0^H V and R~_0^H R, the traces Tr[W^H R] and
+// Tr[W^H W] that give zeta_k, the column norms of the stopping test, the L x L solves for alpha_k
+// and gamma_k, and the block updates
+//   U = (P - zeta V) alpha,  X += zeta F + G,  R -= zeta W + Y,  P = R + U gamma,  V = W + Y gamma.
+//
+// A block is N rows of L complex numbers (row n at n*L).  Every kernel walks rows in chunks of
+// CH rows with a fixed chunk -> block assignment (block b takes chunks b, b + grid, ...), stages the
+// chunk in shared memory, and accumulates its share of the reductions in a fixed order.  Each
+// block writes its partial sums to a slot of `part`; a one-block finalize kernel adds the slots in
+// block order.  Results are therefore bitwise reproducible from run to run (no float atomics).
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+constexpr int TS_THREADS = 256;
+constexpr int CH = 32;                     // rows per chunk
+constexpr int CHE = CH * WD_LMAX;          // complex entries per chunk at most
+
+WD_DEV Cx<double> ld2(const double* p, size_t e) {
+  double2 v = *reinterpret_cast<const double2*>(p + 2 * e);
+  return {v.x, v.y};
+}
+WD_DEV void st2(double* p, size_t e, Cx<double> a) {
+  *reinterpret_cast<double2*>(p + 2 * e) = make_double2(a.re, a.im);
+}
+WD_DEV Cx<double> sm(const double2& v) { return {v.x, v.y}; }
+WD_DEV double2 d2(Cx<double> a) { return make_double2(a.re, a.im); }
+
+// Gram accumulation over one staged chunk: thread t < L*L owns entry (a, b) = (t / L, t % L) of
+// A^H B; thread t < L also accumulates ||B_col t||^2 when `norms`.
+WD_DEV void gram_chunk(const double2* As, const double2* Bs, int rows, int L, Cx<double>& acc,
+                       double& nacc, bool norms) {
+  const int t = threadIdx.x;
+  if (t < L * L) {
+    const int a = t / L, b = t - (t / L) * L;
+    for (int n = 0; n < rows; ++n) acc = cfmaj(sm(As[n * L + a]), sm(Bs[n * L + b]), acc);
+  }
+  if (norms && t < L)
+    for (int n = 0; n < rows; ++n) nacc += cnorm2(sm(Bs[n * L + t]));
+}
+
+WD_DEV void write_partial(double2* part, int L, Cx<double> acc, double nacc, bool norms) {
+  const int t = threadIdx.x;
+  double2* p = part + (size_t)blockIdx.x * PART_STRIDE;
+  if (t < L * L) p[t] = d2(acc);
+  if (norms && t < L) p[WD_LMAX * WD_LMAX + t] = make_double2(nacc, 0.0);
+}
+
+// ---------------------------------------------------------------- Gram A^H B (+ norms of B)
+__global__ void __launch_bounds__(TS_THREADS)
+gram_kernel(const double* __restrict__ A, const double* __restrict__ B, int L, long long rows,
+            double2* __restrict__ part, bool norms) {
+  __shared__ double2 As[CHE], Bs[CHE];
+  Cx<double> acc = czero<double>();
+  double nacc = 0.0;
+  const long long nchunks = (rows + CH - 1) / CH;
+  for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+    const long long r0 = ck * CH;
+    const int nr = (int)min((long long)CH, rows - r0);
+    const int cnt = nr * L;
+    const size_t e0 = (size_t)r0 * L;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      As[e] = d2(ld2(A, e0 + e));
+      Bs[e] = d2(ld2(B, e0 + e));
+    }
+    __syncthreads();
+    gram_chunk(As, Bs, nr, L, acc, nacc, norms);
+    __syncthreads();
+  }
+  write_partial(part, L, acc, nacc, norms);
+}
+
+// Column norms ||A_col||^2 only.
+__global__ void __launch_bounds__(TS_THREADS)
+colnorm_kernel(const double* __restrict__ A, int L, long long rows, double2* __restrict__ part) {
+  __shared__ double red[TS_THREADS];
+  // thread t handles column t % L of rows strided by (TS_THREADS / L) within a chunk
+  const int per = TS_THREADS / L;
+  const int col = threadIdx.x % L, lane_row = threadIdx.x / L;
+  double acc = 0.0;
+  if (lane_row < per) {
+    const long long nchunks = (rows + CH - 1) / CH;
+    for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+      const long long r0 = ck * CH;
+      const int nr = (int)min((long long)CH, rows - r0);
+      for (int n = lane_row; n < nr; n += per) acc += cnorm2(ld2(A, (size_t)(r0 + n) * L + col));
+    }
+  }
+  red[threadIdx.x] = (lane_row < per) ? acc : 0.0;
+  __syncthreads();
+  if (threadIdx.x < L) {
+    double s = 0.0;
+    for (int k = 0; k < per; ++k) s += red[k * L + threadIdx.x];
+    part[(size_t)blockIdx.x * PART_STRIDE + WD_LMAX * WD_LMAX + threadIdx.x] = make_double2(s, 0.0);
+  }
+}
+
+// Tr[W^H R] and Tr[W^H W] over all N*L entries.
+__global__ void __launch_bounds__(TS_THREADS)
+trace_kernel(const double* __restrict__ W, const double* __restrict__ R, long long count,
+             double2* __restrict__ part) {
+  __shared__ double red[3][TS_THREADS];
+  Cx<double> wr = czero<double>();
+  double ww = 0.0;
+  const long long per_block = (long long)CH * WD_LMAX;
+  const long long nchunks = (count + per_block - 1) / per_block;
+  for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+    const long long e0 = ck * per_block;
+    const long long e1 = min(count, e0 + per_block);
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const Cx<double> w = ld2(W, e), r = ld2(R, e);
+      wr = cfmaj(w, r, wr);
+      ww += cnorm2(w);
+    }
+  }
+  red[0][threadIdx.x] = wr.re;
+  red[1][threadIdx.x] = wr.im;
+  red[2][threadIdx.x] = ww;
+  __syncthreads();
+  for (int off = TS_THREADS / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off)
+      for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double2* p = part + (size_t)blockIdx.x * PART_STRIDE;
+    p[0] = make_double2(red[0][0], red[1][0]);
+    p[1] = make_double2(red[2][0], 0.0);
+  }
+}
+
+// Sum the per-block partials in block order.  which: GRAM_* target, -1 none; norms_out: where the
+// column norms go (may be null); traces: finalize Tr[W^H R], Tr[W^H W] instead.
+__global__ void finalize_kernel(const double2* __restrict__ part, int nblocks, int L,
+                                SolverState* st, int which, double* norms_out, bool traces) {
+  const int t = threadIdx.x;
+  if (traces) {
+    if (t < 2) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int b = 0; b < nblocks; ++b) {
+        const double2 v = part[(size_t)b * PART_STRIDE + t];
+        s.x += v.x;
+        s.y += v.y;
+      }
+      if (t == 0) st->trwr = s; else st->trww = s.x;
+    }
+    return;
+  }
+  if (which >= 0 && t < L * L) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = 0; b < nblocks; ++b) {
+      const double2 v = part[(size_t)b * PART_STRIDE + t];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    double2* dst = which == GRAM_RTR ? st->rtr : which == GRAM_RTR_NEW ? st->rtr_new : st->rtv;
+    dst[t] = s;
+  }
+  if (norms_out && t < L) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * PART_STRIDE + WD_LMAX * WD_LMAX + t].x;
+    norms_out[t] = s;
+  }
+}
+
+// ---------------------------------------------------------------- L x L solves (one warp)
+// Solves C Z = Rhs in place: M is the augmented L x 2L matrix [C | Rhs] in shared memory,
+// row-major with leading dimension 2*WD_LMAX.  Partial pivoting by the largest modulus.  Returns
+// true when the system is singular in the sense of the oracle: a pivot that is not finite or whose
+// modulus is below 1e-13 times the largest pivot modulus.
+constexpr double PIVOT_RTOL = 1e-13;
+constexpr int LD = 2 * WD_LMAX;
+
+__device__ bool lu_solve_warp(Cx<double>* M, int L) {
+  const int lane = threadIdx.x;
+  double pmax = 0.0, pmin = 1e308;
+  bool bad = false;
+  for (int k = 0; k < L; ++k) {
+    int p = k;
+    double best = cnorm2(M[k * LD + k]);
+    for (int i = k + 1; i < L; ++i) {
+      const double v = cnorm2(M[i * LD + k]);
+      if (v > best) { best = v; p = i; }
+    }
+    __syncwarp();
+    if (p != k && lane < 2 * L) {
+      const Cx<double> tmp = M[k * LD + lane];
+      M[k * LD + lane] = M[p * LD + lane];
+      M[p * LD + lane] = tmp;
+    }
+    __syncwarp();
+    const Cx<double> piv = M[k * LD + k];
+    const double pa = sqrt(cnorm2(piv));
+    if (!isfinite(pa) || pa == 0.0) bad = true;
+    pmax = fmax(pmax, pa);
+    pmin = fmin(pmin, pa);
+    const double pn = cnorm2(piv);
+    const Cx<double> rp = cmake(piv.re / pn, -piv.im / pn);
+    for (int i = k + 1; i < L; ++i) {
+      const Cx<double> f = cmul(M[i * LD + k], rp);
+      __syncwarp();
+      if (lane > k && lane < 2 * L) M[i * LD + lane] = M[i * LD + lane] - cmul(f, M[k * LD + lane]);
+      if (lane == k) M[i * LD + k] = f;
+      __syncwarp();
+    }
+  }
+  if (!(pmin >= PIVOT_RTOL * pmax)) bad = true;
+  // back substitution, one right-hand-side column per lane
+  if (lane >= L && lane < 2 * L) {
+    for (int i = L - 1; i >= 0; --i) {
+      Cx<double> v = M[i * LD + lane];
+      for (int jj = i + 1; jj < L; ++jj) v = v - cmul(M[i * LD + jj], M[jj * LD + lane]);
+      const Cx<double> d = M[i * LD + i];
+      const double dn = cnorm2(d);
+      M[i * LD + lane] = cmul(v, cmake(d.re / dn, -d.im / dn));
+    }
+  }
+  __syncwarp();
+  return bad;
+}
+
+// alpha_k from (R~_0^H V_k) alpha_k = R~_0^H R_k, and zeta_k = Tr[W^H R] / Tr[W^H W].
+__global__ void solve_alpha_kernel(SolverState* st, int L) {
+  __shared__ Cx<double> M[WD_LMAX * LD];
+  if (st->status != ST_OK) return;
+  const int lane = threadIdx.x;
+  for (int i = 0; i < L; ++i)
+    if (lane < L) {
+      M[i * LD + lane] = sm(st->rtv[i * L + lane]);
+      M[i * LD + L + lane] = sm(st->rtr[i * L + lane]);
+    }
+  __syncwarp();
+  const bool bad = lu_solve_warp(M, L);
+  if (lane < L)
+    for (int i = 0; i < L; ++i) st->alpha[i * L + lane] = bad ? make_double2(0, 0) : d2(M[i * LD + L + lane]);
+  if (lane == 0) {
+    const double ww = st->trww;
+    const Cx<double> wr = sm(st->trwr);
+    Cx<double> z = cmake(wr.re / ww, wr.im / ww);
+    bool zbad = !(ww > 0.0) || !isfinite(z.re) || !isfinite(z.im);
+    st->zeta = zbad ? make_double2(0, 0) : d2(z);
+    if (bad) st->status = ST_ALPHA_SINGULAR;
+    else if (zbad) st->status = ST_ZETA_BAD;
+  }
+}
+
+// gamma_k from (R~_0^H R_k) gamma_k = R~_0^H R_{k+1} / zeta_k; then R~_0^H R_k <- R~_0^H R_{k+1}.
+__global__ void solve_gamma_kernel(SolverState* st, int L) {
+  __shared__ Cx<double> M[WD_LMAX * LD];
+  if (st->status != ST_OK) return;
+  const int lane = threadIdx.x;
+  const Cx<double> z = sm(st->zeta);
+  const double zn = cnorm2(z);
+  const Cx<double> rz = cmake(z.re / zn, -z.im / zn);
+  for (int i = 0; i < L; ++i)
+    if (lane < L) {
+      M[i * LD + lane] = sm(st->rtr[i * L + lane]);
+      M[i * LD + L + lane] = cmul(sm(st->rtr_new[i * L + lane]), rz);
+    }
+  __syncwarp();
+  const bool bad = lu_solve_warp(M, L);
+  if (lane < L)
+    for (int i = 0; i < L; ++i) {
+      st->gamma[i * L + lane] = bad ? make_double2(0, 0) : d2(M[i * LD + L + lane]);
+      st->rtr[i * L + lane] = st->rtr_new[i * L + lane];
+    }
+  if (lane == 0 && bad) st->status = ST_GAMMA_SINGULAR;
+}
+
+// ---------------------------------------------------------------- block updates
+// U = (P - zeta V) alpha  (S_k of the algorithm box is never stored).
+__global__ void __launch_bounds__(TS_THREADS)
+update_u_kernel(const double* __restrict__ P, const double* __restrict__ V, double* __restrict__ U,
+                int L, long long rows, const SolverState* __restrict__ st) {
+  __shared__ double2 Ss[CHE];
+  __shared__ double2 al[WD_LMAX * WD_LMAX];
+  if (st->status != ST_OK) return;
+  const Cx<double> z = sm(st->zeta);
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) al[e] = st->alpha[e];
+  const long long nchunks = (rows + CH - 1) / CH;
+  for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+    const long long r0 = ck * CH;
+    const int nr = (int)min((long long)CH, rows - r0);
+    const int cnt = nr * L;
+    const size_t e0 = (size_t)r0 * L;
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x)
+      Ss[e] = d2(ld2(P, e0 + e) - cmul(z, ld2(V, e0 + e)));
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int n = e / L, b = e - (e / L) * L;
+      Cx<double> acc = czero<double>();
+      for (int a = 0; a < L; ++a) acc = cfma(sm(Ss[n * L + a]), sm(al[a * L + b]), acc);
+      st2(U, e0 + e, acc);
+    }
+  }
+}
+
+// X += zeta F + G;  R -= zeta W + Y;  partial R~_0^H R_{k+1} and ||r_i||^2.
+__global__ void __launch_bounds__(TS_THREADS)
+update_xr_kernel(double* __restrict__ X, const double* __restrict__ F, const double* __restrict__ G,
+                 double* __restrict__ R, const double* __restrict__ W, const double* __restrict__ Y,
+                 const double* __restrict__ Rt, int L, long long rows, double2* __restrict__ part,
+                 const SolverState* __restrict__ st) {
+  __shared__ double2 As[CHE], Bs[CHE];
+  if (st->status != ST_OK) return;
+  const Cx<double> z = sm(st->zeta);
+  Cx<double> acc = czero<double>();
+  double nacc = 0.0;
+  const long long nchunks = (rows + CH - 1) / CH;
+  for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+    const long long r0 = ck * CH;
+    const int nr = (int)min((long long)CH, rows - r0);
+    const int cnt = nr * L;
+    const size_t e0 = (size_t)r0 * L;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const size_t q = e0 + e;
+      const Cx<double> x = ld2(X, q) + cmul(z, ld2(F, q)) + ld2(G, q);
+      const Cx<double> r = ld2(R, q) - cmul(z, ld2(W, q)) - ld2(Y, q);
+      st2(X, q, x);
+      st2(R, q, r);
+      Bs[e] = d2(r);
+      As[e] = d2(ld2(Rt, q));
+    }
+    __syncthreads();
+    gram_chunk(As, Bs, nr, L, acc, nacc, true);
+    __syncthreads();
+  }
+  write_partial(part, L, acc, nacc, true);
+}
+
+// P = R + U gamma;  V = W + Y gamma;  partial R~_0^H V_{k+1}.
+__global__ void __launch_bounds__(TS_THREADS)
+update_pv_kernel(double* __restrict__ P, double* __restrict__ V, const double* __restrict__ R,
+                 const double* __restrict__ W, const double* __restrict__ U,
+                 const double* __restrict__ Y, const double* __restrict__ Rt, int L, long long rows,
+                 double2* __restrict__ part, const SolverState* __restrict__ st) {
+  __shared__ double2 Us[CHE], Ys[CHE], Vs[CHE], Rs[CHE];
+  __shared__ double2 ga[WD_LMAX * WD_LMAX];
+  if (st->status != ST_OK) return;
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) ga[e] = st->gamma[e];
+  Cx<double> acc = czero<double>();
+  double nacc = 0.0;
+  const long long nchunks = (rows + CH - 1) / CH;
+  for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+    const long long r0 = ck * CH;
+    const int nr = (int)min((long long)CH, rows - r0);
+    const int cnt = nr * L;
+    const size_t e0 = (size_t)r0 * L;
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      Us[e] = d2(ld2(U, e0 + e));
+      Ys[e] = d2(ld2(Y, e0 + e));
+      Rs[e] = d2(ld2(Rt, e0 + e));
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int n = e / L, b = e - (e / L) * L;
+      Cx<double> pu = czero<double>(), py = czero<double>();
+      for (int a = 0; a < L; ++a) {
+        const Cx<double> gm = sm(ga[a * L + b]);
+        pu = cfma(sm(Us[n * L + a]), gm, pu);
+        py = cfma(sm(Ys[n * L + a]), gm, py);
+      }
+      const size_t q = e0 + e;
+      st2(P, q, ld2(R, q) + pu);
+      const Cx<double> v = ld2(W, q) + py;
+      st2(V, q, v);
+      Vs[e] = d2(v);
+    }
+    __syncthreads();
+    gram_chunk(Rs, Vs, nr, L, acc, nacc, false);
+  }
+  write_partial(part, L, acc, nacc, false);
+}
+
+inline int blocks_for(long long rows) {
+  const long long nchunks = (rows + CH - 1) / CH;
+  const long long cap = 152LL * 4;
+  return (int)(nchunks < cap ? (nchunks > 0 ? nchunks : 1) : cap);
+}
+
+}  // namespace
+
+int ts_blocks(long long rows) { return blocks_for(rows); }
+
+cudaError_t launch_gram(const double* A, const double* B, int L, long long rows, double2* part,
+                        SolverState* st, int which, bool norms_of_b, cudaStream_t s) {
+  const int nb = blocks_for(rows);
+  gram_kernel<<<nb, TS_THREADS, 0, s>>>(A, B, L, rows, part, norms_of_b);
+  finalize_kernel<<<1, WD_LMAX * WD_LMAX, 0, s>>>(part, nb, L, st, which,
+                                                  norms_of_b ? st->rnorm2 : nullptr, false);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colnorms(const double* A, int L, long long rows, double2* part,
+                            double* out_norm2, cudaStream_t s) {
+  const int nb = blocks_for(rows);
+  colnorm_kernel<<<nb, TS_THREADS, 0, s>>>(A, L, rows, part);
+  finalize_kernel<<<1, WD_LMAX * WD_LMAX, 0, s>>>(part, nb, L, nullptr, -1, out_norm2, false);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_traces(const double* W, const double* R, int L, long long rows,
+                          double2* part, SolverState* st, cudaStream_t s) {
+  const int nb = blocks_for(rows);
+  trace_kernel<<<nb, TS_THREADS, 0, s>>>(W, R, rows * L, part);
+  finalize_kernel<<<1, WD_LMAX * WD_LMAX, 0, s>>>(part, nb, L, st, -1, nullptr, true);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_alpha(SolverState* st, int L, cudaStream_t s) {
+  solve_alpha_kernel<<<1, 32, 0, s>>>(st, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_gamma(SolverState* st, int L, cudaStream_t s) {
+  solve_gamma_kernel<<<1, 32, 0, s>>>(st, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_u(const double* P, const double* V, double* U, int L, long long rows,
+                            const SolverState* st, cudaStream_t s) {
+  update_u_kernel<<<blocks_for(rows), TS_THREADS, 0, s>>>(P, V, U, L, rows, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_xr(double* X, const double* F, const double* G, double* R,
+                             const double* W, const double* Y, const double* Rt, int L,
+                             long long rows, double2* part, SolverState* st, cudaStream_t s) {
+  const int nb = blocks_for(rows);
+  update_xr_kernel<<<nb, TS_THREADS, 0, s>>>(X, F, G, R, W, Y, Rt, L, rows, part, st);
+  finalize_kernel<<<1, WD_LMAX * WD_LMAX, 0, s>>>(part, nb, L, st, GRAM_RTR_NEW, st->rnorm2, false);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_pv(double* P, double* V, const double* R, const double* W,
+                             const double* U, const double* Y, const double* Rt, int L,
+                             long long rows, double2* part, SolverState* st, cudaStream_t s) {
+  const int nb = blocks_for(rows);
+  update_pv_kernel<<<nb, TS_THREADS, 0, s>>>(P, V, R, W, U, Y, Rt, L, rows, part, st);
+  finalize_kernel<<<1, WD_LMAX * WD_LMAX, 0, s>>>(part, nb, L, st, GRAM_RTV, nullptr, false);
+  return cudaGetLastError();
+}

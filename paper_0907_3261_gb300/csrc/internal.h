@@ -1,0 +1,74 @@
+// Internal interfaces between the translation units of the library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+#ifndef WD_LMAX
+#define WD_LMAX 16
+#endif
+
+// The operator A on the device.  FP64 fields are always present; FP32 copies serve the
+// FP32 preconditioner.
+struct Op {
+  Geom g;
+  double kappa, csw;
+  double* links;     // [V][4][3][3] complex
+  double* clov;      // [V][2][36]  A_D blocks, packed Hermitian
+  double* clov_inv;  // [V][2][36]  A_D^{-1} blocks
+  float* links32;
+  float* clov_inv32;
+};
+
+// ---- dslash.cu (FP64)
+cudaError_t launch_apply_f64(const Op& op, const double* x, double* y, int L, cudaStream_t st);
+cudaError_t launch_resid_f64(const Op& op, const double* x, const double* b, double* y, int L,
+                             cudaStream_t st);
+cudaError_t launch_jacobi_f64(const Op& op, const double* g_in, const double* u, double* g_out,
+                              int L, cudaStream_t st);
+cudaError_t launch_site_inverse_f64(const Op& op, const double* u, double* g_out, int L,
+                                    cudaStream_t st);
+
+// ---- clover.cu
+// Builds clov and clov_inv from links; *singular_dev receives 1 if some 6x6 block is singular.
+cudaError_t launch_clover_build(const Op& op, int* singular_dev, cudaStream_t st);
+
+// ---- blas.cu: tall-skinny N x L operations with deterministic reductions
+struct SolverState {
+  double2 rtv[WD_LMAX * WD_LMAX];      // R~_0^H V_k
+  double2 rtr[WD_LMAX * WD_LMAX];      // R~_0^H R_k
+  double2 rtr_new[WD_LMAX * WD_LMAX];  // R~_0^H R_{k+1}
+  double2 alpha[WD_LMAX * WD_LMAX];
+  double2 gamma[WD_LMAX * WD_LMAX];
+  double2 zeta;
+  double2 trwr;                          // Tr[W^H R]
+  double trww;                           // Tr[W^H W]
+  double rnorm2[WD_LMAX];                // ||r_i||^2 of the latest R
+  int status;                            // 0, or ST_* below
+};
+enum { ST_OK = 0, ST_ALPHA_SINGULAR = 1, ST_GAMMA_SINGULAR = 2, ST_ZETA_BAD = 3 };
+
+// Partial-sum slots per block of the reduction kernels.
+constexpr int PART_STRIDE = WD_LMAX * WD_LMAX + WD_LMAX;
+int ts_blocks(long long rows);   // grid size of the tall-skinny kernels for `rows` rows
+
+// Which L x L result a gram pass writes.
+enum { GRAM_RTR = 0, GRAM_RTR_NEW = 1, GRAM_RTV = 2 };
+
+cudaError_t launch_gram(const double* A, const double* B, int L, long long rows, double2* part,
+                        SolverState* st, int which, bool norms_of_b, cudaStream_t s);
+cudaError_t launch_colnorms(const double* A, int L, long long rows, double2* part,
+                            double* out_norm2, cudaStream_t s);
+cudaError_t launch_traces(const double* W, const double* R, int L, long long rows,
+                          double2* part, SolverState* st, cudaStream_t s);
+cudaError_t launch_solve_alpha(SolverState* st, int L, cudaStream_t s);
+cudaError_t launch_solve_gamma(SolverState* st, int L, cudaStream_t s);
+cudaError_t launch_update_u(const double* P, const double* V, double* U, int L, long long rows,
+                            const SolverState* st, cudaStream_t s);
+cudaError_t launch_update_xr(double* X, const double* F, const double* G, double* R,
+                             const double* W, const double* Y, const double* Rt, int L,
+                             long long rows, double2* part, SolverState* st, cudaStream_t s);
+cudaError_t launch_update_pv(double* P, double* V, const double* R, const double* W,
+                             const double* U, const double* Y, const double* Rt, int L,
+                             long long rows, double2* part, SolverState* st, cudaStream_t s);

@@ -1,0 +1,236 @@
+"""CUDA path vs the FP64 oracle, through the C-ABI (needs a GB300)."""
+import numpy as np
+import pytest
+
+from oracle import operator as O
+from oracle import solver as S
+from paper_0907_3261_gb300 import inputs as I
+import pins
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+APPLY_TOL = 1e-12     # relative, wd_apply vs oracle
+SOLVE_X_TOL = 1e-9    # ||X - X_oracle|| / ||X||
+TRUE_RES_TOL = 1e-12  # per column
+
+
+@pytest.fixture(scope="module")
+def wd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0907_3261_gb300 as pkg
+    return pkg
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def max_elem_rel(a, b):
+    """Largest entry-wise difference relative to the largest entry of the reference."""
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+class GpuOp:
+    """The CUDA operator behind the pins' interface (apply only)."""
+
+    def __init__(self, wd, links, dims, kappa, csw):
+        self.ctx = wd.wd_create(dev(links), dims, kappa, csw)
+        self.wd = wd
+
+    def apply(self, psi):
+        return host(self.wd.wd_apply(self.ctx, dev(psi)))
+
+
+CASES = [((4, 4, 4, 4), 4, 0.3, 0.115, 1.0),     # the 4^4 point-source workload
+         ((2, 2, 2, 2), 3, 0.5, 0.125, 1.3),     # forward and backward neighbours coincide
+         ((3, 4, 5, 6), 5, 0.6, 0.13, 1.7),      # odd extents, ragged last block
+         ((8, 8, 8, 16), 12, 0.2, 0.12, 1.0),    # 8^3 x 16, L = 12
+         ((4, 4, 4, 8), 1, 0.3, 0.12, 1.0),      # L = 1
+         ((2, 4, 2, 4), 16, 0.4, 0.12, 1.0)]     # L = WD_LMAX
+
+
+@pytest.mark.parametrize("dims,L,eps,kappa,csw", CASES)
+def test_wd_apply_matches_oracle(wd, dims, L, eps, kappa, csw):
+    links = I.random_links(dims, eps, seed=0)
+    op = O.WilsonClover(links, dims, kappa, csw)
+    X = I.gaussian_block(dims, L, seed=3)
+    ctx = wd.wd_create(dev(links), dims, kappa, csw)
+    Y = host(wd.wd_apply(ctx, dev(X)))
+    Y_ref = op.apply(X)
+    assert rel(Y, Y_ref) <= APPLY_TOL
+    assert max_elem_rel(Y, Y_ref) <= APPLY_TOL
+
+
+def test_wd_apply_host_buffers_match_device(wd):
+    dims = (3, 4, 5, 6)
+    links = I.random_links(dims, 0.5, seed=1)
+    X = I.gaussian_block(dims, 6, seed=4)
+    ctx = wd.wd_create(links, dims, 0.12, 1.2)           # links from host memory
+    Yh = wd.wd_apply(ctx, X)                              # host in, host out
+    Yd = host(wd.wd_apply(ctx, dev(X)))
+    assert np.array_equal(Yh, Yd)
+
+
+def test_gpu_operator_satisfies_pins(wd):
+    make = lambda U, d, k, c: GpuOp(wd, U, d, k, c)
+    assert pins.free_field_error(make) < 1e-13
+    assert pins.free_field_error(make, dims=(3, 5, 4, 6), n=(1, 2, 1, 5)) < 1e-13
+    assert pins.gamma5_hermiticity_error(make) < 1e-13
+    assert pins.gauge_covariance_error(make) < 1e-13
+
+
+@pytest.mark.parametrize("j", [0, 1, 2, 5])
+@pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 4), ((3, 4, 5, 6), 7)])
+def test_jacobi_matches_oracle(wd, j, dims, L):
+    links = I.random_links(dims, 0.4, seed=2)
+    op = O.WilsonClover(links, dims, 0.12, 1.0)
+    R = I.gaussian_block(dims, L, seed=5)
+    ctx = wd.wd_create(dev(links), dims, 0.12, 1.0)
+    G = host(wd.jacobi_precond(ctx, dev(R), j))
+    G_ref = S.jacobi(op, R, j)
+    assert rel(G, G_ref) <= APPLY_TOL
+    assert max_elem_rel(G, G_ref) <= APPLY_TOL
+
+
+@pytest.mark.parametrize("B_kind,L,j", [("point", 4, 4), ("z4", 4, 0), ("z4", 3, 2),
+                                        ("z4", 12, 4), ("z4", 1, 3)])
+def test_solve_matches_oracle_4_4(wd, B_kind, L, j):
+    dims = (4, 4, 4, 4)
+    links = I.random_links(dims, 0.3, seed=0)
+    op = O.WilsonClover(links, dims, 0.115, 1.0)
+    B = I.point_sources(dims, L) if B_kind == "point" else I.z4_noise(dims, L, seed=1)
+    ref = S.solve(op, B, j=j, tol=1e-12)
+    ctx = wd.wd_create(dev(links), dims, 0.115, 1.0)
+    Xg, info = wd.bbicggr_solve(ctx, dev(B), j=j, tol=1e-12)
+    Xg = host(Xg)
+    assert info["status"] == wd.WD_OK
+    assert abs(info["iters"] - ref.iters) <= 1
+    if info["restarts"] == 0:
+        assert info["mvm_paper"] == L * (2 * (j + 1) * info["iters"] + 1)
+    assert S.true_residual(op, B, Xg).max() <= TRUE_RES_TOL
+    assert info["max_true_resid"] <= TRUE_RES_TOL
+    assert rel(Xg, ref.X) <= SOLVE_X_TOL
+
+
+@pytest.mark.parametrize("j,L", [(0, 1), (2, 4), (4, 12)])
+def test_solve_matches_dense_lu_2_4(wd, j, L):
+    dims = (2, 2, 2, 2)
+    links = I.random_links(dims, 0.3, seed=0)
+    op = O.WilsonClover(links, dims, 0.115, 1.0)
+    B = I.z4_noise(dims, L, seed=1)
+    X_lu = np.linalg.solve(op.dense(), B.reshape(op.N, L)).reshape(B.shape)
+    ctx = wd.wd_create(dev(links), dims, 0.115, 1.0)
+    Xg, info = wd.bbicggr_solve(ctx, dev(B), j=j, tol=1e-12)
+    assert info["status"] == wd.WD_OK
+    assert rel(host(Xg), X_lu) <= SOLVE_X_TOL
+
+
+def test_solve_history_matches_oracle(wd):
+    """The per-iteration max relative residual follows the oracle's to rounding."""
+    dims = (4, 4, 4, 4)
+    links = I.random_links(dims, 0.3, seed=0)
+    op = O.WilsonClover(links, dims, 0.12, 1.0)
+    B = I.z4_noise(dims, 4, seed=1)
+    X, st, k, nm, rec, hist = S.bbicggr(op, B, np.zeros_like(B), 3, 1e-12)
+    ctx = wd.wd_create(dev(links), dims, 0.12, 1.0)
+    _, info = wd.bbicggr_solve(ctx, dev(B), j=3, tol=1e-12, max_restarts=0, history=1000)
+    h = info["history"]
+    n = min(len(h), len(hist))
+    assert n >= 5
+    # the residual curve agrees while it is well above the rounding floor
+    for a, b in zip(h[:n], hist[:n]):
+        if b > 1e-9:
+            assert abs(a - b) <= 1e-6 * b
+
+
+def test_solve_8_8_8_16_true_residual(wd):
+    dims = (8, 8, 8, 16)
+    links = I.random_links(dims, 0.2, seed=0)
+    op = O.WilsonClover(links, dims, 0.12, 1.0)
+    B = I.z4_noise(dims, 12, seed=1)
+    ctx = wd.wd_create(dev(links), dims, 0.12, 1.0)
+    Xg, info = wd.bbicggr_solve(ctx, dev(B), j=4, tol=1e-12)
+    assert info["status"] == wd.WD_OK
+    assert S.true_residual(op, B, host(Xg)).max() <= TRUE_RES_TOL
+
+
+def test_solve_host_buffers_and_determinism(wd):
+    dims = (4, 4, 4, 8)
+    links = I.random_links(dims, 0.3, seed=3)
+    B = I.z4_noise(dims, 6, seed=2)
+    ctx = wd.wd_create(dev(links), dims, 0.12, 1.0)
+    X1, i1 = wd.bbicggr_solve(ctx, B, j=3, tol=1e-12)          # host numpy in and out
+    X2, i2 = wd.bbicggr_solve(ctx, dev(B), j=3, tol=1e-12)
+    X3, i3 = wd.bbicggr_solve(ctx, dev(B), j=3, tol=1e-12)
+    assert i1["status"] == i2["status"] == wd.WD_OK
+    assert np.array_equal(X1, host(X2))                     # reductions are deterministic
+    assert np.array_equal(host(X2), host(X3))
+    assert i1["iters"] == i2["iters"] == i3["iters"]
+
+
+def test_solver_error_paths(wd):
+    dims = (2, 2, 2, 4)
+    links = I.random_links(dims, 0.3, seed=0)
+    op = O.WilsonClover(links, dims, 0.115, 1.0)
+    ctx = wd.wd_create(dev(links), dims, 0.115, 1.0)
+    B = I.z4_noise(dims, 2, seed=1)
+    # maxit
+    ref = S.bbicggr(op, B, np.zeros_like(B), 1, 1e-12, maxit=2)
+    _, info = wd.bbicggr_solve(ctx, dev(B), j=1, tol=1e-12, maxit=2, max_restarts=0)
+    assert info["status"] == wd.WD_NOT_CONVERGED == ref[1] and info["iters"] == 2
+    # divergence threshold
+    ref = S.bbicggr(op, B, np.zeros_like(B), 1, 1e-12, div_thresh=1e-6)
+    _, info = wd.bbicggr_solve(ctx, dev(B), j=1, tol=1e-12, div_thresh=1e-6)
+    assert info["status"] == wd.WD_DIVERGED == ref[1] and info["iters"] == ref[2] == 1
+    # rank-deficient block: singular R~_0^H V_0 (rank loss) -> BREAKDOWN before any update
+    B2 = B.copy()
+    B2[..., 1] = B2[..., 0]
+    ref = S.bbicggr(op, B2, np.zeros_like(B2), 1, 1e-12)
+    X2, info = wd.bbicggr_solve(ctx, dev(B2), j=1, tol=1e-12)
+    assert info["status"] == wd.WD_BREAKDOWN == ref[1] and info["iters"] == ref[2] == 0
+    assert np.array_equal(host(X2), np.zeros_like(B2))
+    # a zero column of B is rejected
+    B3 = B.copy()
+    B3[..., 0] = 0
+    with pytest.raises(wd.WDError):
+        wd.bbicggr_solve(ctx, dev(B3), j=1, tol=1e-12)
+    # bad arguments
+    with pytest.raises(wd.WDError):
+        wd.bbicggr_solve(ctx, dev(I.z4_noise(dims, 17, seed=1)), j=1)
+    with pytest.raises(wd.WDError):
+        wd.wd_create(dev(links), (1, 2, 2, 4), 0.1, 1.0)
+    with pytest.raises(wd.WDError):
+        wd.bbicggr_solve(ctx, dev(B), j=-1)
+
+
+def test_full_size_16_16_16_32(wd):
+    """16^3 x 32, L = 12 (the paper's lattice, the bench workload): wd_apply against the oracle
+    on every site, gamma_5-hermiticity of the CUDA operator, and a solve whose true residual the
+    oracle recomputes."""
+    dims = (16, 16, 16, 32)
+    links = I.random_links(dims, 0.2, seed=0)
+    kappa = 0.12
+    ctx = wd.wd_create(dev(links), dims, kappa, 1.0)
+    X = I.z4_noise(dims, 12, seed=7)
+    Y = host(wd.wd_apply(ctx, dev(X)))
+    op = O.WilsonClover(links, dims, kappa, 1.0)
+    Y_ref = op.apply(X)
+    assert rel(Y, Y_ref) <= APPLY_TOL
+    del Y, Y_ref
+    B = I.z4_noise(dims, 12, seed=1)
+    Xg, info = wd.bbicggr_solve(ctx, dev(B), j=12, tol=1e-12)
+    assert info["status"] == wd.WD_OK
+    assert S.true_residual(op, B, host(Xg)).max() <= TRUE_RES_TOL
