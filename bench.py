@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Time-to-solution of preconditioned block BiCGGR (arXiv:0907.3261) on one or more GB300s.
+
+Workload (the paper's lattice, Sec. 3.1, with synthetic links in place of its configurations):
+16^3 x 32 periodic lattice, links SU3proj(1 + 0.2 G) (seed 0), c_SW = 1.0, kappa = 0.134, L = 12
+Z4-noise sources (seed 1 + rank), Jacobi j = 12 (the paper's recommended L = 12, j >= 12, Sec. 3.3),
+X_0 = 0, R~_0 = R_0, tolerance 1e-12 on the recursive residual and then on the true residual.
+One step = one complete solve through the C-ABI.  kappa = 0.134 is the largest value of the
+0.001-step sweep from 0.115 at which the L = 1, j = 0 solve still converges (660 iterations);
+at 0.135 it no longer does.
+
+Prints one JSON line on stdout.  --impl reference times the FP64 oracle on the host cores instead.
+With torchrun each rank solves its own sources (independent problems, no collective on the data
+path); the timing is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (16, 16, 16, 32)
+L_RHS = 12
+J_JACOBI = 12
+KAPPA = 0.134
+CSW = 1.0
+LINK_EPS = 0.2
+TOL = 1e-12
+# Outer iterations block BiCGGR takes on this workload (L = 12, j = 12, kappa = 0.134): used only
+# by the reference arm, which cannot run the full oracle solve, to scale its per-MVM time.
+WORKLOAD_ITERS = 36
+
+METRIC = "time-to-solution at true resid 1e-12 for L RHS; Dslash HBM GB/s vs peak"
+FLOP_APPLY = 1824          # flop per site per RHS of A (1320 hopping + 504 clover)
+FLOP_JACOBI = 1872         # flop per site per RHS of one Jacobi sweep A_D^{-1}(U + kappa H G)
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
+
+
+def algorithmic_bytes(kind: str, L: int, real_bytes: int = 8) -> int:
+    """Minimum DRAM bytes per site: 4 links (each link serves two sites), one packed 2x(6x6)
+    clover or inverse block, and the spinors read or written once."""
+    links = 4 * 18 * real_bytes
+    clov = 72 * real_bytes
+    spinor = 24 * real_bytes * L
+    if kind == "dslash_apply":
+        return links + clov + 2 * spinor
+    if kind == "dslash_jacobi":
+        return links + clov + 3 * spinor
+    raise ValueError(kind)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ---------------------------------------------------------------- clocks during the timed region
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200", "-i",
+                                       gpu_id], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(", ") for r in self.f.read().splitlines() if r.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for_smi(torch, dev) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev.index or 0)
+
+
+# ---------------------------------------------------------------- traffic from committed ncu summaries
+def csrc_sha() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_0907_3261_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class: str, precision: str):
+    """DRAM bytes per launch recorded in profiles/*.md as
+    ``bench-traffic: <class> <precision> <bytes> <csrc sha>``; None if absent or stale."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    sha = csrc_sha()
+    for name in os.listdir(pdir):
+        if not name.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(pdir, name)):
+            m = re.match(r"\s*bench-traffic:\s*(\S+)\s+(\S+)\s+(\d+)\s+(\S+)", line)
+            if m and m.group(1) == kernel_class and m.group(2) == precision:
+                return int(m.group(3)) if m.group(4) == sha else None
+    return None
+
+
+# ---------------------------------------------------------------- oracle timing (host cores)
+def oracle_sample(L: int):
+    """Time the oracle's A and A_D^{-1} on a 16^3 x 8 slab of the workload (a quarter of the
+    lattice, periodic) and scale to the full lattice.  Returns (t_apply, t_inverse, cores)."""
+    import numpy as np
+    from oracle import operator as O
+    from paper_0907_3261_gb300 import inputs as I
+    slab = (DIMS[0], DIMS[1], DIMS[2], DIMS[3] // 4)
+    links = I.random_links(DIMS, LINK_EPS, seed=0)[: int(np.prod(slab))]
+    op = O.WilsonClover(links, slab, KAPPA, CSW)
+    X = I.z4_noise(slab, L, seed=1)
+    c0, w0 = time.process_time(), time.perf_counter()
+    op.apply(X)
+    w1 = time.perf_counter()
+    op.apply_site_diagonal(X, inverse=True)
+    w2 = time.perf_counter()
+    c1 = time.process_time()
+    cores = max(1, round((c1 - c0) / max(w2 - w0, 1e-9)))
+    return 4 * (w1 - w0), 4 * (w2 - w1), cores
+
+
+def oracle_tts(k: int, j: int, t_apply: float, t_inv: float) -> float:
+    """Oracle time for a solve of k outer iterations: 2k + 1 products with A (R_0, W_0, the
+    Y_k and W_{k+1}), 2k applications of M of j sweeps (each one A product and one A_D^{-1}), and
+    the true residual at exit.  The L x L Gram and update steps are not included."""
+    return (2 * k + 2) * t_apply + 2 * j * k * (t_apply + t_inv)
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    vals = []
+    cores = 1
+    for step in range(args.warmup + args.steps):
+        t_apply, t_inv, cores = oracle_sample(L_RHS)
+        v = oracle_tts(WORKLOAD_ITERS, J_JACOBI, t_apply, t_inv)
+        if step >= args.warmup:
+            vals.append(v)
+        log(f"reference step {step}: apply {t_apply:.2f}s inverse {t_inv:.2f}s -> {v:.1f}s")
+    value = statistics.mean(vals)
+    sample = (f"oracle A and A_D^-1 on a 16^3x8 slab (L=12), scaled x4 to 16^3x32 and by the "
+              f"solve's MVM count for k={WORKLOAD_ITERS} outer iterations, j={J_JACOBI}")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
+           "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def config(args):
+    return {"workload": f"clover Wilson-Dirac {DIMS[0]}^3x{DIMS[3]}, L={L_RHS} Z4 sources, "
+                        f"Jacobi j={J_JACOBI}, kappa={KAPPA}, c_SW={CSW}, "
+                        f"links SU3proj(1+{LINK_EPS}G), true resid <= {TOL}",
+            "lattice": list(DIMS), "L": L_RHS, "j": J_JACOBI, "kappa": KAPPA, "csw": CSW,
+            "tol": TOL, "precision": args.precision,
+            "parallelism": f"independent solves x{args.gpus}",
+            "l2": "working set 13 blocks x 302 MB > L2 (no flush needed)"}
+
+
+# ---------------------------------------------------------------- GB300 arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_0907_3261_gb300 as wd
+    from paper_0907_3261_gb300 import inputs as I
+    prec = {"fp64": 0}[args.precision]
+
+    links = torch.from_numpy(I.random_links(DIMS, LINK_EPS, seed=0)).to(dev)
+    Bh = torch.from_numpy(I.z4_noise(DIMS, L_RHS, seed=1 + rank)).pin_memory()
+    B = Bh.to(dev)
+    ctx = wd.wd_create(links, DIMS, KAPPA, CSW)
+    X = torch.zeros_like(B)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve():
+        X.zero_()
+        return wd.bbicggr_solve(ctx, B, X, j=J_JACOBI, tol=TOL, precision=prec, stream=stream)[1]
+
+    for w in range(args.warmup):
+        info = solve()
+        log(f"[rank {rank}] warmup {w}: {info['status_name']} k={info['iters']} "
+            f"{info['seconds']:.3f}s true={info['max_true_resid']:.2e}")
+
+    def maxr(v: float) -> float:
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- device-timed region: inputs resident in HBM
+    wd.wd_profile_reset(ctx)
+    wd.wd_profile_enable(ctx, True)
+    sampler = ClockSampler(gpu_id_for_smi(torch, dev))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [solve() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    wd.wd_profile_enable(ctx, False)
+    prof = wd.wd_profile_read(ctx)
+    ms_total = maxr(e0.elapsed_time(e1))
+    ms_step = ms_total / args.steps
+    ok = all(i["status"] == wd.WD_OK and i["max_true_resid"] <= TOL for i in infos)
+
+    # ---- end to end through the C-ABI with pinned host buffers
+    Xh = torch.zeros(B.shape, dtype=torch.complex128).pin_memory()
+    Bn, Xn = Bh.numpy(), Xh.numpy()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Xn[...] = 0
+        _, ie = wd.bbicggr_solve(ctx, Bn, Xn, j=J_JACOBI, tol=TOL, precision=prec)
+        ok = ok and ie["status"] == wd.WD_OK
+    e2e_s = maxr((time.perf_counter() - t0) / args.steps)
+    block = B.numel() * 16
+
+    # ---- roofline of the dominant kernel class
+    dslash = {k: v for k, v in prof.items() if k.startswith("dslash") and v[0] > 0}
+    dom = max(dslash, key=lambda k: dslash[k][1])
+    n_launch, ms_dom = dslash[dom]
+    avg_s = ms_dom / n_launch / 1e3
+    V = int(np.prod(DIMS))
+    flop_unit = FLOP_JACOBI if dom == "dslash_jacobi" else FLOP_APPLY
+    tflops = flop_unit * V * L_RHS / avg_s / 1e12
+    kind = "dslash_jacobi" if dom == "dslash_jacobi" else "dslash_apply"
+    gbs = algorithmic_bytes(kind, L_RHS) * V / avg_s / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = ncu_traffic(dom, args.precision)
+    roofline = {"kernel": dom, "bound": "alu", "achieved": round(tflops, 4),
+                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                "flop_per_site_rhs": flop_unit, "avg_launch_ms": round(avg_s * 1e3, 4),
+                "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(gbs / hbm_peak, 4),
+                        "bytes_per_launch": algorithmic_bytes(kind, L_RHS) * V}}
+    apply_n, apply_ms = prof.get("dslash_apply", (0, 0.0))
+    if apply_n:
+        a_s = apply_ms / apply_n / 1e3
+        a_gbs = algorithmic_bytes("dslash_apply", L_RHS) * V / a_s / 1e9
+        roofline["dslash_apply"] = {"avg_launch_ms": round(a_s * 1e3, 4),
+                                    "tflops": round(FLOP_APPLY * V * L_RHS / a_s / 1e12, 4),
+                                    "hbm_gbs": round(a_gbs, 1),
+                                    "hbm_frac": round(a_gbs / hbm_peak, 4)}
+
+    launches = sum(n for k, (n, _) in prof.items())
+    out = {"metric": METRIC, "value": round(ms_step / 1e3, 6), "unit": "s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "config": config(args),
+           "roofline": roofline,
+           "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": 2 * block,
+                   "d2h_bytes_per_step": block},
+           "gpu_launches": launches, "clocks": clocks,
+           "solve": {"status": "ok" if ok else "FAILED", "iters": infos[-1]["iters"],
+                     "mvm_paper": infos[-1]["mvm_paper"],
+                     "max_true_resid": max(i["max_true_resid"] for i in infos),
+                     "restarts": infos[-1]["restarts"]},
+           "kernels": {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in prof.items() if n or ms}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_apply, t_inv, cores = oracle_sample(L_RHS)
+        k = infos[-1]["iters"]
+        out["cpu_baseline"] = {
+            "value": round(oracle_tts(k, J_JACOBI, t_apply, t_inv), 3), "unit": "s",
+            "cores": cores, "kind": "oracle",
+            "sample": (f"oracle A ({t_apply:.2f}s) and A_D^-1 ({t_inv:.2f}s) on the full lattice, "
+                       f"timed on a 16^3x8 slab and scaled x4, times the MVMs of this run's "
+                       f"k={k} iterations at j={J_JACOBI}; L x L steps not included")}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    wd.wd_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+    return 0 if ok else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())

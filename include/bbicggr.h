@@ -118,6 +118,32 @@ void bbicggr_default_opts(bbicggr_opts* opts);
 const char* wd_strerror(int code);
 const char* wd_last_error(void);
 
+/* Per-kernel instrumentation.  Every kernel launch of a context is counted per kernel class
+ * (WD_K_*).  With timing on, each launch is also bracketed by two CUDA events recorded on the
+ * launching stream, and the elapsed device times are summed when the call that launched them
+ * returns.  wd_profile_read gives the launch count and summed milliseconds of one class since the
+ * last wd_profile_reset; wd_profile_name its name. */
+enum {
+  WD_K_APPLY = 0,      /* dslash Y = A X */
+  WD_K_RESID,          /* dslash R = B - A X */
+  WD_K_JACOBI,         /* dslash Jacobi sweep G <- A_D^{-1}(U + kappa H G) */
+  WD_K_SITE_INV,       /* first Jacobi sweep G = A_D^{-1} U */
+  WD_K_UPDATE_U,       /* U = (P - zeta V) alpha */
+  WD_K_UPDATE_XR,      /* X += zeta F + G, R -= zeta W + Y, R~_0^H R, ||r_i||^2 */
+  WD_K_UPDATE_PV,      /* P = R + U gamma, V = W + Y gamma, R~_0^H V */
+  WD_K_GRAM,           /* standalone Gram product */
+  WD_K_TRACE,          /* Tr[W^H R], Tr[W^H W] */
+  WD_K_SOLVE_LL,       /* L x L LU solves */
+  WD_K_COLNORM,        /* column norms */
+  WD_K_COPY,           /* device-to-device block copies */
+  WD_K_CONVERT,        /* FP64 <-> FP32 conversions of the FP32 preconditioner */
+  WD_K_COUNT
+};
+int wd_profile_enable(wd_ctx* ctx, int timing_on);
+int wd_profile_reset(wd_ctx* ctx);
+int wd_profile_read(const wd_ctx* ctx, int kernel_class, long long* launches, double* ms);
+const char* wd_profile_name(int kernel_class);
+
 /* Lattice size and parameters of a context (for bindings): dims[4], V, kappa, c_SW. */
 int wd_query(const wd_ctx* ctx, int dims[4], long long* volume, double* kappa, double* csw);
 

@@ -5,7 +5,8 @@ The compute path is the CUDA library ``libbbicggr.so`` (sources in ``csrc/``, C-
 ``inputs`` holds the seeded synthetic input generators.
 """
 from ._lib import (WD_BREAKDOWN, WD_DIVERGED, WD_LMAX, WD_NOT_CONVERGED, WD_OK, Context, WDError,
-                   bbicggr_solve, jacobi_precond, wd_apply, wd_create, wd_destroy)
+                   bbicggr_solve, jacobi_precond, wd_apply, wd_create, wd_destroy,
+                   wd_profile_enable, wd_profile_read, wd_profile_reset)
 
 __all__ = ["wd_create", "wd_destroy", "wd_apply", "jacobi_precond", "bbicggr_solve", "Context",
-           "WDError", "WD_OK", "WD_NOT_CONVERGED", "WD_DIVERGED", "WD_BREAKDOWN", "WD_LMAX"]
+           "WDError", "wd_profile_enable", "wd_profile_read", "wd_profile_reset", "WD_OK", "WD_NOT_CONVERGED", "WD_DIVERGED", "WD_BREAKDOWN", "WD_LMAX"]

@@ -77,7 +77,13 @@ def lib():
     L.wd_last_error.restype = C.c_char_p
     L.wd_query.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(d),
                            C.POINTER(d)]
-    for name in ("wd_create", "wd_apply", "jacobi_precond", "bbicggr_solve", "wd_query"):
+    L.wd_profile_enable.argtypes = [vp, i]
+    L.wd_profile_reset.argtypes = [vp]
+    L.wd_profile_read.argtypes = [vp, i, C.POINTER(C.c_longlong), C.POINTER(d)]
+    L.wd_profile_name.argtypes = [i]
+    L.wd_profile_name.restype = C.c_char_p
+    for name in ("wd_create", "wd_apply", "jacobi_precond", "bbicggr_solve", "wd_query",
+                 "wd_profile_enable", "wd_profile_reset", "wd_profile_read"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -230,3 +236,26 @@ def bbicggr_solve(ctx: Context, B, X=None, j: int = 12, tol: float = 1e-12, maxi
                rec_resid=np.array(rec[:]), true_resid=np.array(tru[:]),
                history=np.array(hist[:info.history_count]), seconds=info.seconds)
     return X, out
+
+
+WD_K_COUNT = 13
+
+
+def wd_profile_enable(ctx: Context, timing_on: bool = True) -> None:
+    """Count kernel launches per class; with timing_on also time them with CUDA events."""
+    _check(lib().wd_profile_enable(ctx.handle, int(bool(timing_on))))
+
+
+def wd_profile_reset(ctx: Context) -> None:
+    _check(lib().wd_profile_reset(ctx.handle))
+
+
+def wd_profile_read(ctx: Context) -> dict:
+    """{kernel class name: (kernel launches, summed device ms)} since the last reset."""
+    out = {}
+    for k in range(WD_K_COUNT):
+        n = C.c_longlong()
+        ms = C.c_double()
+        _check(lib().wd_profile_read(ctx.handle, k, C.byref(n), C.byref(ms)))
+        out[lib().wd_profile_name(k).decode()] = (int(n.value), float(ms.value))
+    return out

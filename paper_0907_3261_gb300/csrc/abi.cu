@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/bbicggr.h"
 #include "internal.h"
@@ -36,6 +37,13 @@ void set_err(const char* fmt, ...) {
       set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
       return e_ == cudaErrorMemoryAllocation ? WD_ENOMEM : WD_ECUDA;                  \
     }                                                                                 \
+  } while (0)
+
+// Launch under the per-kernel instrumentation (needs `c` and `s` in scope).
+#define LAUNCH(cls, nkernels, call)         \
+  do {                                      \
+    Timed timed_(c, cls, nkernels, s);      \
+    CU(call);                               \
   } while (0)
 
 #define CHECK(rc)              \
@@ -81,8 +89,21 @@ struct HostMirror {
 
 }  // namespace
 
+struct Prof {
+  bool timing = false;
+  long long kernels[WD_K_COUNT] = {};
+  double ms[WD_K_COUNT] = {};
+  struct Pending {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+};
+
 struct wd_ctx {
   Op op{};
+  Prof prof;
   int device = 0;
   // solver workspace for the current L
   int L = 0;
@@ -100,6 +121,53 @@ namespace {
 enum { B_X, B_R, B_P, B_V, B_W, B_F, B_U, B_G, B_Y, B_RT, B_T, B_B, B_XS, B_COUNT };
 
 size_t block_bytes(const wd_ctx* c, int L) { return (size_t)c->op.g.V * 12 * L * 16; }
+
+cudaEvent_t prof_event(wd_ctx* c) {
+  if (!c->prof.pool.empty()) {
+    cudaEvent_t e = c->prof.pool.back();
+    c->prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Counts the kernels of one launcher call of class `cls` and, with timing on, brackets them with
+// two events on the launching stream.
+struct Timed {
+  wd_ctx* c;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  Timed(wd_ctx* c_, int cls_, int nkernels, cudaStream_t s_) : c(c_), cls(cls_), s(s_) {
+    c->prof.kernels[cls] += nkernels;
+    if (c->prof.timing && (a = prof_event(c)) != nullptr) cudaEventRecord(a, s);
+  }
+  ~Timed() {
+    if (!a) return;
+    cudaEvent_t b = prof_event(c);
+    if (!b) { c->prof.pool.push_back(a); return; }
+    cudaEventRecord(b, s);
+    c->prof.pending.push_back({cls, a, b});
+  }
+};
+
+// Adds the elapsed times of all bracketed launches (waits for them).
+void harvest(wd_ctx* c) {
+  for (auto& p : c->prof.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+      c->prof.ms[p.cls] += ms;
+    cudaGetLastError();
+    c->prof.pool.push_back(p.a);
+    c->prof.pool.push_back(p.b);
+  }
+  c->prof.pending.clear();
+}
 
 int check_L(int L) {
   if (L < 1 || L > WD_LMAX) {
@@ -156,15 +224,15 @@ int precondition(wd_ctx* c, const double* R, double* a, double* b, double** res,
                  long long* hop_count, cudaStream_t s) {
   const Op& op = c->op;
   if (j == 0) {
-    CU(cudaMemcpyAsync(a, R, block_bytes(c, L), cudaMemcpyDeviceToDevice, s));
+    LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(a, R, block_bytes(c, L), cudaMemcpyDeviceToDevice, s));
     *res = a;
     return WD_OK;
   }
-  CU(launch_site_inverse_f64(op, R, a, L, s));
+  LAUNCH(WD_K_SITE_INV, 1, launch_site_inverse_f64(op, R, a, L, s));
   double* cur = a;
   double* nxt = b;
   for (int i = 1; i < j; ++i) {
-    CU(launch_jacobi_f64(op, cur, R, nxt, L, s));
+    LAUNCH(WD_K_JACOBI, 1, launch_jacobi_f64(op, cur, R, nxt, L, s));
     if (hop_count) ++*hop_count;
     double* t = cur;
     cur = nxt;
@@ -221,11 +289,11 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, double tol,
   CU(cudaMemsetAsync(&st->status, 0, sizeof(int), s));
 
   // R_0 = B - A X_0;  P_0 = R_0;  R~_0 = R_0
-  CU(launch_resid_f64(op, X, B, R, L, s));
+  LAUNCH(WD_K_RESID, 1, launch_resid_f64(op, X, B, R, L, s));
   ++*hop_count;
-  CU(cudaMemcpyAsync(P, R, bytes, cudaMemcpyDeviceToDevice, s));
-  CU(cudaMemcpyAsync(Rt, R, bytes, cudaMemcpyDeviceToDevice, s));
-  CU(launch_gram(Rt, R, L, rows, part, st, GRAM_RTR, true, s));
+  LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(P, R, bytes, cudaMemcpyDeviceToDevice, s));
+  LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(Rt, R, bytes, cudaMemcpyDeviceToDevice, s));
+  LAUNCH(WD_K_GRAM, 2, launch_gram(Rt, R, L, rows, part, st, GRAM_RTR, true, s));
   CHECK(read_back(c, s));
   double m = max_rel(c->hm->rnorm2, b2, L, out->rec);
   out->k = 0;
@@ -237,22 +305,22 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, double tol,
   double* res;
   CHECK(precondition(c, R, pF, pT, &res, L, j, hop_count, s));
   if (res != pF) { pT = pF; pF = res; }
-  CU(launch_apply_f64(op, pF, W, L, s));
+  LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pF, W, L, s));
   ++*hop_count;
-  CU(cudaMemcpyAsync(V, W, bytes, cudaMemcpyDeviceToDevice, s));
-  CU(launch_traces(W, R, L, rows, part, st, s));
-  CU(launch_gram(Rt, V, L, rows, part, st, GRAM_RTV, false, s));
+  LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(V, W, bytes, cudaMemcpyDeviceToDevice, s));
+  LAUNCH(WD_K_TRACE, 2, launch_traces(W, R, L, rows, part, st, s));
+  LAUNCH(WD_K_GRAM, 2, launch_gram(Rt, V, L, rows, part, st, GRAM_RTV, false, s));
 
   int k = 0;
   for (;;) {
     if (k >= maxit) { out->status = WD_NOT_CONVERGED; break; }
-    CU(launch_solve_alpha(st, L, s));                       // alpha_k, zeta_k
-    CU(launch_update_u(P, V, U, L, rows, st, s));           // U_k = (P_k - zeta_k V_k) alpha_k
+    LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_alpha(st, L, s));                       // alpha_k, zeta_k
+    LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(P, V, U, L, rows, st, s));           // U_k = (P_k - zeta_k V_k) alpha_k
     CHECK(precondition(c, U, pG, pT, &res, L, j, hop_count, s));   // G_k = M U_k
     if (res != pG) { pT = pG; pG = res; }
-    CU(launch_apply_f64(op, pG, Y, L, s));                  // Y_k = A G_k
+    LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pG, Y, L, s));                  // Y_k = A G_k
     ++*hop_count;
-    CU(launch_update_xr(X, pF, pG, R, W, Y, Rt, L, rows, part, st, s));   // X_{k+1}, R_{k+1}
+    LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(X, pF, pG, R, W, Y, Rt, L, rows, part, st, s));   // X_{k+1}, R_{k+1}
     CHECK(read_back(c, s));
     if (c->hm->status != ST_OK) { out->status = WD_BREAKDOWN; break; }
     ++k;
@@ -263,11 +331,11 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, double tol,
     if (m > div_thresh) { out->status = WD_DIVERGED; break; }
     CHECK(precondition(c, R, pF, pT, &res, L, j, hop_count, s));   // F_{k+1} = M R_{k+1}
     if (res != pF) { pT = pF; pF = res; }
-    CU(launch_apply_f64(op, pF, W, L, s));                  // W_{k+1} = A F_{k+1}
+    LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pF, W, L, s));                  // W_{k+1} = A F_{k+1}
     ++*hop_count;
-    CU(launch_traces(W, R, L, rows, part, st, s));          // Tr[W^H R], Tr[W^H W]
-    CU(launch_solve_gamma(st, L, s));                       // gamma_k
-    CU(launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s));   // P_{k+1}, V_{k+1}
+    LAUNCH(WD_K_TRACE, 2, launch_traces(W, R, L, rows, part, st, s));          // Tr[W^H R], Tr[W^H W]
+    LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_gamma(st, L, s));                       // gamma_k
+    LAUNCH(WD_K_UPDATE_PV, 2, launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s));   // P_{k+1}, V_{k+1}
   }
   out->k = k;
   return WD_OK;
@@ -310,6 +378,8 @@ const char* wd_last_error(void) { return g_err; }
 
 void wd_destroy(wd_ctx* c) {
   if (!c) return;
+  harvest(c);
+  for (auto e : c->prof.pool) cudaEventDestroy(e);
   cudaFree(c->op.links);
   cudaFree(c->op.clov);
   cudaFree(c->op.clov_inv);
@@ -385,6 +455,34 @@ int wd_create(wd_ctx** out, const void* links, const int dims[4], double kappa, 
   return WD_OK;
 }
 
+int wd_profile_enable(wd_ctx* c, int timing_on) {
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  harvest(c);
+  c->prof.timing = timing_on != 0;
+  return WD_OK;
+}
+
+int wd_profile_reset(wd_ctx* c) {
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  harvest(c);
+  for (int i = 0; i < WD_K_COUNT; ++i) { c->prof.kernels[i] = 0; c->prof.ms[i] = 0.0; }
+  return WD_OK;
+}
+
+int wd_profile_read(const wd_ctx* c, int cls, long long* launches, double* ms) {
+  if (!c || cls < 0 || cls >= WD_K_COUNT) { set_err("bad context or kernel class"); return WD_EINVAL; }
+  if (launches) *launches = c->prof.kernels[cls];
+  if (ms) *ms = c->prof.ms[cls];
+  return WD_OK;
+}
+
+const char* wd_profile_name(int cls) {
+  static const char* names[WD_K_COUNT] = {
+      "dslash_apply", "dslash_resid", "dslash_jacobi", "site_inverse", "update_u", "update_xr",
+      "update_pv", "gram", "trace", "solve_ll", "colnorm", "copy", "convert"};
+  return (cls >= 0 && cls < WD_K_COUNT) ? names[cls] : "unknown";
+}
+
 int wd_query(const wd_ctx* c, int dims[4], long long* volume, double* kappa, double* csw) {
   if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
   if (dims) for (int m = 0; m < 4; ++m) dims[m] = c->op.g.d[m];
@@ -407,9 +505,10 @@ int wd_apply(wd_ctx* c, const void* X, void* Y, int L, void* stream) {
   const bool y_dev = is_device_ptr(Y);
   double* yd = static_cast<double*>(Y);
   if (!y_dev) { CHECK(c->stage_out.ensure(bytes)); yd = c->stage_out.d(); }
-  CU(launch_apply_f64(c->op, xd, yd, L, s));
+  LAUNCH(WD_K_APPLY, 1, launch_apply_f64(c->op, xd, yd, L, s));
   if (!y_dev) CU(cudaMemcpyAsync(Y, yd, bytes, cudaMemcpyDeviceToHost, s));
   if (staged_x || !y_dev) CU(cudaStreamSynchronize(s));
+  harvest(c);
   return WD_OK;
 }
 
@@ -437,9 +536,10 @@ int jacobi_precond(wd_ctx* c, const void* R, void* G, int L, int j, int precisio
   double* first = (j % 2 == 1) ? gd : tmp;
   double* second = (j % 2 == 1) ? tmp : gd;
   CHECK(precondition(c, rd, first, second, &res, L, j, nullptr, s));
-  if (res != gd) CU(cudaMemcpyAsync(gd, res, bytes, cudaMemcpyDeviceToDevice, s));
+  if (res != gd) LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(gd, res, bytes, cudaMemcpyDeviceToDevice, s));
   if (!g_dev) CU(cudaMemcpyAsync(G, gd, bytes, cudaMemcpyDeviceToHost, s));
   if (staged_r || !g_dev) CU(cudaStreamSynchronize(s));
+  harvest(c);
   return WD_OK;
 }
 
@@ -477,7 +577,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     CU(cudaMemcpyAsync(Xd, X, bytes, cudaMemcpyHostToDevice, s));
   }
   double b2[WD_LMAX];
-  CU(launch_colnorms(Bd, L, rows, static_cast<double2*>(c->part.p), c->bnorm2_dev, s));
+  LAUNCH(WD_K_COLNORM, 2, launch_colnorms(Bd, L, rows, static_cast<double2*>(c->part.p), c->bnorm2_dev, s));
   CU(cudaMemcpyAsync(b2, c->bnorm2_dev, L * sizeof(double), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   for (int i = 0; i < L; ++i)
@@ -500,10 +600,10 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     mvm_paper += (long long)L * (2LL * (j + 1) * rr.k + 1);
     // true residual ||b_i - A x_i|| / ||b_i||
     double* T = c->blk[B_T].d();
-    CU(launch_resid_f64(c->op, Xd, Bd, T, L, s));
+    LAUNCH(WD_K_RESID, 1, launch_resid_f64(c->op, Xd, Bd, T, L, s));
     ++hops;
     double t2[WD_LMAX];
-    CU(launch_colnorms(T, L, rows, static_cast<double2*>(c->part.p), c->bnorm2_dev + WD_LMAX, s));
+    LAUNCH(WD_K_COLNORM, 2, launch_colnorms(T, L, rows, static_cast<double2*>(c->part.p), c->bnorm2_dev + WD_LMAX, s));
     CU(cudaMemcpyAsync(t2, c->bnorm2_dev + WD_LMAX, L * sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     mtrue = max_rel(t2, b2, L, true_rel);
@@ -532,6 +632,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     info->history_count = hist_n;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
+  harvest(c);
   if (status != WD_OK)
     set_err("bbicggr_solve: %s after %d iterations (max recursive residual %.3e, true %.3e)",
             wd_strerror(status), iters, info ? info->max_rec_resid : 0.0, mtrue);
