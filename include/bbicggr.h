@@ -105,6 +105,23 @@ int wd_apply(wd_ctx* ctx, const void* X, void* Y, int L, void* stream);
  * 1 = FP32 sweeps).  R and G must not overlap. */
 int jacobi_precond(wd_ctx* ctx, const void* R, void* G, int L, int j, int precision, void* stream);
 
+/* jacobi_precond_noalloc: the same G = M R as jacobi_precond (FP64 sweeps), computed without
+ * allocating any memory.  The paper has no counterpart; this exists for callers that cannot let a
+ * library call cudaMalloc -- a framework whose caching allocator already owns the free device
+ * memory, or a latency-bound loop that cannot pay for cudaMalloc/cudaFree and the device
+ * synchronisation cudaFree implies.  jacobi_precond takes its ping-pong block from the context's
+ * solver workspace (allocated on first use); this variant takes it from a file-scope device array
+ * of 32 MiB, which every GPU that loads the library holds until the process exits.
+ *   Limits: 12*V*L <= 2,097,152 complex numbers (e.g. 8^3x16 with L <= 21, 16^3x32 does not fit);
+ *   larger blocks return WD_EINVAL.  R and G must be device buffers (WD_EINVAL for host memory,
+ *   which would need staging) and must not overlap.
+ *   Set-up: the first call on a device, with that device current, looks up the array's device
+ *   address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Sharing: every call on a device uses the same array, which keeps the last call's contents (the
+ *   sweeps overwrite it before reading it, so nothing needs clearing).  Calls whose GPU work
+ *   overlaps -- on different streams, or from different host threads -- race on the array. */
+int jacobi_precond_noalloc(wd_ctx* ctx, const void* R, void* G, int L, int j, void* stream);
+
 /* Preconditioned block BiCGGR (Sec. 2, algorithm box) with the j-step Jacobi preconditioner,
  * R~_0 = R_0 (Sec. 3.3).  X holds X_0 on entry (zero it for the paper's X_0 = 0) and the solution
  * on exit.  Iterates until max_i ||r_i||/||b_i|| <= tol on the recursive residual, checked after

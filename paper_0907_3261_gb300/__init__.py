@@ -5,6 +5,7 @@ The compute path is the CUDA library ``libbbicggr.so`` (sources in ``csrc/``, C-
 ``inputs`` holds the seeded synthetic input generators.
 """
 from ._lib import (WD_BREAKDOWN, WD_DIVERGED, WD_LMAX, WD_NOT_CONVERGED, WD_OK, Context, WDError,
+                   jacobi_precond_noalloc,
                    bbicggr_solve, jacobi_precond, wd_apply, wd_create, wd_destroy,
                    wd_profile_enable, wd_profile_read, wd_profile_reset)
 

@@ -69,6 +69,7 @@ def lib():
     L.wd_apply.argtypes = [vp, vp, vp, i, vp]
     L.jacobi_precond.argtypes = [vp, vp, vp, i, i, i, vp]
     L.bbicggr_solve.argtypes = [vp, vp, vp, i, i, d, C.POINTER(Opts), C.POINTER(Info), vp]
+    L.jacobi_precond_noalloc.argtypes = [vp, vp, vp, i, i, vp]
     L.bbicggr_default_opts.argtypes = [C.POINTER(Opts)]
     L.bbicggr_default_opts.restype = None
     L.wd_strerror.argtypes = [i]
@@ -82,7 +83,8 @@ def lib():
     L.wd_profile_read.argtypes = [vp, i, C.POINTER(C.c_longlong), C.POINTER(d)]
     L.wd_profile_name.argtypes = [i]
     L.wd_profile_name.restype = C.c_char_p
-    for name in ("wd_create", "wd_apply", "jacobi_precond", "bbicggr_solve", "wd_query",
+    for name in ("wd_create", "wd_apply", "jacobi_precond", "jacobi_precond_noalloc",
+                 "bbicggr_solve", "wd_query",
                  "wd_profile_enable", "wd_profile_reset", "wd_profile_read"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -194,6 +196,15 @@ def jacobi_precond(ctx: Context, R, j: int, G=None, precision: int = 0, stream=N
         G = _empty_like(R)
     pg, _, kg = _ptr_and_L(G, "G")
     _check(lib().jacobi_precond(ctx.handle, pr, pg, L, int(j), int(precision), _stream(stream)))
+    return G
+
+
+def jacobi_precond_noalloc(ctx: Context, R, G, j: int, stream=None):
+    """G = M R like jacobi_precond, for device buffers, allocating nothing (a static 32 MiB
+    scratch array in the library replaces the workspace block)."""
+    pr, L, kr = _ptr_and_L(R, "R")
+    pg, _, kg = _ptr_and_L(G, "G")
+    _check(lib().jacobi_precond_noalloc(ctx.handle, pr, pg, L, int(j), _stream(stream)))
     return G
 
 

@@ -349,6 +349,15 @@ __global__ void to_float_kernel(const double* __restrict__ a, float* __restrict_
 
 }  // namespace
 
+const Op* wd_ctx_op(const wd_ctx* c) { return &c->op; }
+
+void wd_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
 extern "C" {
 
 void bbicggr_default_opts(bbicggr_opts* o) {

@@ -72,3 +72,8 @@ cudaError_t launch_update_xr(double* X, const double* F, const double* G, double
 cudaError_t launch_update_pv(double* P, double* V, const double* R, const double* W,
                              const double* U, const double* Y, const double* Rt, int L,
                              long long rows, double2* part, SolverState* st, cudaStream_t s);
+
+// ---- abi.cu helpers for other translation units
+struct wd_ctx;
+const Op* wd_ctx_op(const wd_ctx* ctx);
+void wd_set_error(const char* fmt, ...);
