@@ -219,7 +219,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -243,7 +243,7 @@ def main():
         dist.barrier()
     import paper_0907_3261_gb300 as wd
     from paper_0907_3261_gb300 import inputs as I
-    prec = {"fp64": 0}[args.precision]
+    prec = {"fp64": 0, "mixed": 1}[args.precision]
 
     links = torch.from_numpy(I.random_links(DIMS, LINK_EPS, seed=0)).to(dev)
     Bh = torch.from_numpy(I.z4_noise(DIMS, L_RHS, seed=1 + rank)).pin_memory()
@@ -302,53 +302,62 @@ def main():
     e2e_s = maxr((time.perf_counter() - t0) / args.steps)
     block = B.numel() * 16
 
-    # ---- roofline of the dominant kernel class
-    dslash = {k: v for k, v in prof.items() if k.startswith("dslash") and v[0] > 0}
-    dom = max(dslash, key=lambda k: dslash[k][1])
-    n_launch, ms_dom = dslash[dom]
-    avg_s = ms_dom / n_launch / 1e3
+    # ---- roofline of the dominant kernel class, and of every stencil class
     V = int(np.prod(DIMS))
-    flop_unit = FLOP_JACOBI if dom == "dslash_jacobi" else FLOP_APPLY
-    tflops = flop_unit * V * L_RHS / avg_s / 1e12
-    kind = "dslash_jacobi" if dom == "dslash_jacobi" else "dslash_apply"
-    gbs = algorithmic_bytes(kind, L_RHS) * V / avg_s / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    traffic = ncu_traffic(dom, args.precision)
-    roofline = {"kernel": dom, "bound": "alu", "achieved": round(tflops, 4),
-                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
-                "flop_per_site_rhs": flop_unit, "avg_launch_ms": round(avg_s * 1e3, 4),
-                "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                        "frac": round(gbs / hbm_peak, 4),
-                        "bytes_per_launch": algorithmic_bytes(kind, L_RHS) * V}}
-    apply_n, apply_ms = prof.get("dslash_apply", (0, 0.0))
-    if apply_n:
-        a_s = apply_ms / apply_n / 1e3
-        a_gbs = algorithmic_bytes("dslash_apply", L_RHS) * V / a_s / 1e9
-        roofline["dslash_apply"] = {"avg_launch_ms": round(a_s * 1e3, 4),
-                                    "tflops": round(FLOP_APPLY * V * L_RHS / a_s / 1e12, 4),
-                                    "hbm_gbs": round(a_gbs, 1),
-                                    "hbm_frac": round(a_gbs / hbm_peak, 4)}
+    fp32_sweeps = args.precision == "mixed"
+    per_kernel = {}
+    for cls in ("dslash_jacobi", "dslash_apply"):
+        n, ms = prof.get(cls, (0, 0.0))
+        if not n:
+            continue
+        avg_s = ms / n / 1e3
+        f32 = cls == "dslash_jacobi" and fp32_sweeps
+        flop_unit = FLOP_JACOBI if cls == "dslash_jacobi" else FLOP_APPLY
+        nbytes = algorithmic_bytes(cls, L_RHS, 4 if f32 else 8) * V
+        tflops = flop_unit * V * L_RHS / avg_s / 1e12
+        gbs = nbytes / avg_s / 1e9
+        if f32:
+            fig = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                   "frac": round(gbs / hbm_peak, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                   "tflops_fp32": round(tflops, 3)}
+        else:
+            fig = {"bound": "alu", "achieved": round(tflops, 4),
+                   "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                   "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                   "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                   "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                           "frac": round(gbs / hbm_peak, 4)}}
+        fig.update({"kernel": cls, "precision": "fp32" if f32 else "fp64",
+                    "traffic": ncu_traffic(cls, "fp32" if f32 else "fp64"),
+                    "algorithmic_bytes_per_launch": nbytes, "flop_per_site_rhs": flop_unit,
+                    "avg_launch_ms": round(avg_s * 1e3, 4), "launches": n,
+                    "total_ms": round(ms, 2)})
+        per_kernel[cls] = fig
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["total_ms"])
+    roofline = dict(per_kernel[dom])
+    roofline["stencil_kernels"] = per_kernel
 
     launches = sum(n for k, (n, _) in prof.items())
+    tile = wd.wd_tuned_tile(ctx, L_RHS)
     out = {"metric": METRIC, "value": round(ms_step / 1e3, 6), "unit": "s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64", "data": "synthetic", "config": config(args),
-           "roofline": roofline,
+           "dtype": "f64" if prec == 0 else "f64+f32", "data": "synthetic",
+           "config": dict(config(args), fp32_sweep_tile=tile), "roofline": roofline,
            "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": 2 * block,
                    "d2h_bytes_per_step": block},
            "gpu_launches": launches, "clocks": clocks,
            "solve": {"status": "ok" if ok else "FAILED", "iters": infos[-1]["iters"],
                      "mvm_paper": infos[-1]["mvm_paper"],
                      "max_true_resid": max(i["max_true_resid"] for i in infos),
-                     "restarts": infos[-1]["restarts"]},
+                     "restarts": infos[-1]["restarts"],
+                     "fallbacks": infos[-1]["fallbacks"]},
            "kernels": {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in prof.items() if n or ms}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_apply, t_inv, cores = oracle_sample(L_RHS)

@@ -67,6 +67,12 @@ typedef struct {
                              FP64 */
   double* history;        /* optional host array: max_i ||r_i||/||b_i|| after every R update */
   int history_len;        /* capacity of history (entries beyond it are dropped) */
+  int stall_window;       /* precision 1 only: when the max relative residual has not reached a new
+                             minimum for this many iterations, or the FP32-preconditioned run breaks
+                             down or diverges, the solve starts over from X_0 with the FP64
+                             preconditioner (block BiCGGR needs a fixed linear M, and FP32
+                             rounding of M can stall it near the critical kappa).  Default 16;
+                             0 disables the fallback.  Costs one more N x L block of workspace */
 } bbicggr_opts;
 
 /* Solve report.  rec_resid and true_resid, when not NULL, are caller-owned host arrays of L. */
@@ -83,6 +89,7 @@ typedef struct {
   double* true_resid;     /* [L] or NULL */
   int history_count;      /* entries written to opts->history */
   double seconds;         /* wall time of the call (host clock, includes host<->device copies) */
+  int fallbacks;          /* switches from the FP32 to the FP64 preconditioner (0 or 1) */
 } bbicggr_info;
 
 /* Build the operator A for the given links (Sec. 2; kappa and c_SW as in Sec. 3.1).
@@ -160,6 +167,13 @@ int wd_profile_enable(wd_ctx* ctx, int timing_on);
 int wd_profile_reset(wd_ctx* ctx);
 int wd_profile_read(const wd_ctx* ctx, int kernel_class, long long* launches, double* ms);
 const char* wd_profile_name(int kernel_class);
+
+/* Tile of the FP32 Jacobi sweep chosen by the autotuner for this L (RHS per thread, threads per
+ * CTA).  The autotuner times every candidate tile once, at the first FP32 preconditioner call with
+ * a given L, and keeps the fastest in the context.  WD_EINVAL until then. */
+int wd_tuned_tile(const wd_ctx* ctx, int L, int* rhs_per_thread, int* block);
+/* Sets that tile by hand instead (rhs_per_thread 1 or 2 dividing L; block 64, 128 or 256). */
+int wd_set_tile(wd_ctx* ctx, int L, int rhs_per_thread, int block);
 
 /* Lattice size and parameters of a context (for bindings): dims[4], V, kappa, c_SW. */
 int wd_query(const wd_ctx* ctx, int dims[4], long long* volume, double* kappa, double* csw);

@@ -32,7 +32,7 @@ class WDError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("maxit", C.c_int), ("div_thresh", C.c_double), ("max_restarts", C.c_int),
                 ("precision", C.c_int), ("history", C.POINTER(C.c_double)),
-                ("history_len", C.c_int)]
+                ("history_len", C.c_int), ("stall_window", C.c_int)]
 
 
 class Info(C.Structure):
@@ -40,7 +40,7 @@ class Info(C.Structure):
                 ("mvm_paper", C.c_longlong), ("mvm_actual", C.c_longlong),
                 ("max_rec_resid", C.c_double), ("max_true_resid", C.c_double),
                 ("rec_resid", C.POINTER(C.c_double)), ("true_resid", C.POINTER(C.c_double)),
-                ("history_count", C.c_int), ("seconds", C.c_double)]
+                ("history_count", C.c_int), ("seconds", C.c_double), ("fallbacks", C.c_int)]
 
 
 _lib = None
@@ -81,6 +81,10 @@ def lib():
     L.wd_profile_enable.argtypes = [vp, i]
     L.wd_profile_reset.argtypes = [vp]
     L.wd_profile_read.argtypes = [vp, i, C.POINTER(C.c_longlong), C.POINTER(d)]
+    L.wd_tuned_tile.argtypes = [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.wd_tuned_tile.restype = C.c_int
+    L.wd_set_tile.argtypes = [vp, i, i, i]
+    L.wd_set_tile.restype = C.c_int
     L.wd_profile_name.argtypes = [i]
     L.wd_profile_name.restype = C.c_char_p
     for name in ("wd_create", "wd_apply", "jacobi_precond", "jacobi_precond_noalloc",
@@ -210,7 +214,7 @@ def jacobi_precond_noalloc(ctx: Context, R, G, j: int, stream=None):
 
 def bbicggr_solve(ctx: Context, B, X=None, j: int = 12, tol: float = 1e-12, maxit: int = 10000,
                   div_thresh: float = 1e2, max_restarts: int = 3, precision: int = 0,
-                  history: int = 0, stream=None):
+                  history: int = 0, stall_window: int = 16, stream=None):
     """Solve A X = B by preconditioned block BiCGGR.  Returns (X, info dict).
 
     ``X`` (if given) holds X_0 and receives the solution; by default X_0 = 0.  Solver outcomes
@@ -228,6 +232,7 @@ def bbicggr_solve(ctx: Context, B, X=None, j: int = 12, tol: float = 1e-12, maxi
     lib().bbicggr_default_opts(C.byref(o))
     o.maxit, o.div_thresh, o.max_restarts, o.precision = int(maxit), float(div_thresh), \
         int(max_restarts), int(precision)
+    o.stall_window = int(stall_window)
     hist = (C.c_double * max(history, 1))()
     if history:
         o.history = C.cast(hist, C.POINTER(C.c_double))
@@ -245,7 +250,8 @@ def bbicggr_solve(ctx: Context, B, X=None, j: int = 12, tol: float = 1e-12, maxi
                restarts=info.restarts, mvm_paper=info.mvm_paper, mvm_actual=info.mvm_actual,
                max_rec_resid=info.max_rec_resid, max_true_resid=info.max_true_resid,
                rec_resid=np.array(rec[:]), true_resid=np.array(tru[:]),
-               history=np.array(hist[:info.history_count]), seconds=info.seconds)
+               history=np.array(hist[:info.history_count]), seconds=info.seconds,
+               fallbacks=info.fallbacks)
     return X, out
 
 
@@ -270,3 +276,16 @@ def wd_profile_read(ctx: Context) -> dict:
         _check(lib().wd_profile_read(ctx.handle, k, C.byref(n), C.byref(ms)))
         out[lib().wd_profile_name(k).decode()] = (int(n.value), float(ms.value))
     return out
+
+
+def wd_tuned_tile(ctx: Context, L: int):
+    """(RHS per thread, threads per CTA) the autotuner chose for the FP32 sweep, or None."""
+    r, b = C.c_int(), C.c_int()
+    if lib().wd_tuned_tile(ctx.handle, int(L), C.byref(r), C.byref(b)) != WD_OK:
+        return None
+    return int(r.value), int(b.value)
+
+
+def wd_set_tile(ctx: Context, L: int, rhs_per_thread: int, block: int) -> None:
+    """Fix the FP32 sweep's tile for this L instead of autotuning it."""
+    _check(lib().wd_set_tile(ctx.handle, int(L), int(rhs_per_thread), int(block)))

@@ -107,18 +107,23 @@ struct wd_ctx {
   int device = 0;
   // solver workspace for the current L
   int L = 0;
-  DevBuf blk[13];          // X R P V W F U G Y Rt T B Xs
+  DevBuf blk[14];          // X R P V W F U G Y Rt T B Xs X0
   DevBuf part;             // reduction partials
   SolverState* st = nullptr;
   HostMirror* hm = nullptr;
   double* bnorm2_dev = nullptr;
   // staging for host pointers in wd_apply / jacobi_precond
   DevBuf stage_in, stage_out;
+  // FP32 preconditioner blocks: U in FP32 and two sweep buffers
+  DevBuf blk32[3];
+  // autotuned tile of the FP32 sweep per L: RHS per thread and threads per CTA (0 = not tuned)
+  int tile_r[WD_LMAX + 1] = {};
+  int tile_block[WD_LMAX + 1] = {};
 };
 
 namespace {
 
-enum { B_X, B_R, B_P, B_V, B_W, B_F, B_U, B_G, B_Y, B_RT, B_T, B_B, B_XS, B_COUNT };
+enum { B_X, B_R, B_P, B_V, B_W, B_F, B_U, B_G, B_Y, B_RT, B_T, B_B, B_XS, B_X0, B_COUNT };
 
 size_t block_bytes(const wd_ctx* c, int L) { return (size_t)c->op.g.V * 12 * L * 16; }
 
@@ -203,6 +208,49 @@ int ensure_workspace(wd_ctx* c, int L) {
   return WD_OK;
 }
 
+// Picks the FP32 sweep's tile (RHS per thread, threads per CTA) for this lattice and L by timing
+// every candidate on the context's FP32 blocks (zeroed first); the winner is kept in the context.
+int autotune_f32(wd_ctx* c, int L, cudaStream_t s) {
+  static const int cand[][2] = {{1, 64}, {1, 128}, {1, 256}, {2, 64}, {2, 128}, {2, 256}};
+  const size_t bytes = (size_t)c->op.g.V * 12 * L * 8;
+  float* u32 = static_cast<float*>(c->blk32[0].p);
+  float* a = static_cast<float*>(c->blk32[1].p);
+  float* b = static_cast<float*>(c->blk32[2].p);
+  CU(cudaMemsetAsync(u32, 0, bytes, s));
+  CU(cudaMemsetAsync(a, 0, bytes, s));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_i = 0;
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < (int)(sizeof(cand) / sizeof(cand[0])) && err == cudaSuccess; ++i) {
+    if (L % cand[i][0] != 0) continue;
+    err = launch_jacobi_f32_tiled(c->op, a, u32, b, nullptr, L, cand[i][0], cand[i][1], s);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
+      err = launch_jacobi_f32_tiled(c->op, a, u32, b, nullptr, L, cand[i][0], cand[i][1], s);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && ms < best) { best = ms; best_i = i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CU(err);
+  c->tile_r[L] = cand[best_i][0];
+  c->tile_block[L] = cand[best_i][1];
+  return WD_OK;
+}
+
+int ensure_workspace32(wd_ctx* c, int L, cudaStream_t s) {
+  const size_t bytes = (size_t)c->op.g.V * 12 * L * 8;
+  for (auto& b : c->blk32) CHECK(b.ensure(bytes));
+  if (!c->tile_r[L]) CHECK(autotune_f32(c, L, s));
+  return WD_OK;
+}
+
 // Device pointer for an input that may live on the host: copies into `stage` when needed.
 int stage_input(const void* p, size_t bytes, DevBuf& stage, const double** out, bool* staged,
                 cudaStream_t s) {
@@ -218,14 +266,38 @@ int stage_input(const void* p, size_t bytes, DevBuf& stage, const double** out, 
   return WD_OK;
 }
 
-// G = M R with j Jacobi sweeps; `a` and `b` are two scratch blocks, the result pointer is
-// returned in *res (one of a, b).  j = 0 copies R.
+// G = M R with j Jacobi sweeps; `a` and `b` are two FP64 scratch blocks, the result pointer is
+// returned in *res (one of a, b).  j = 0 copies R.  precision 1 runs the sweeps in FP32 (FP32
+// links, FP32 A_D^{-1}, FP32 accumulation) and writes the last one to `a` in FP64.
 int precondition(wd_ctx* c, const double* R, double* a, double* b, double** res, int L, int j,
-                 long long* hop_count, cudaStream_t s) {
+                 int precision, long long* hop_count, cudaStream_t s) {
   const Op& op = c->op;
   if (j == 0) {
     LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(a, R, block_bytes(c, L), cudaMemcpyDeviceToDevice, s));
     *res = a;
+    return WD_OK;
+  }
+  if (precision == 1) {
+    *res = a;
+    if (j == 1) {
+      LAUNCH(WD_K_SITE_INV, 1, launch_site_inverse_mixed(op, R, nullptr, nullptr, a, L, s));
+      return WD_OK;
+    }
+    CHECK(ensure_workspace32(c, L, s));
+    float* u32 = static_cast<float*>(c->blk32[0].p);
+    float* cur = static_cast<float*>(c->blk32[1].p);
+    float* nxt = static_cast<float*>(c->blk32[2].p);
+    LAUNCH(WD_K_SITE_INV, 1, launch_site_inverse_mixed(op, R, u32, cur, nullptr, L, s));
+    for (int i = 1; i < j; ++i) {
+      const bool last = i == j - 1;
+      LAUNCH(WD_K_JACOBI, 1,
+             launch_jacobi_f32_tiled(op, cur, u32, last ? nullptr : nxt, last ? a : nullptr, L,
+                                     c->tile_r[L], c->tile_block[L], s));
+      if (hop_count) ++*hop_count;
+      float* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
     return WD_OK;
   }
   LAUNCH(WD_K_SITE_INV, 1, launch_site_inverse_f64(op, R, a, L, s));
@@ -251,6 +323,8 @@ int read_back(wd_ctx* c, cudaStream_t s) {
   return WD_OK;
 }
 
+constexpr int RUN_STALLED = 100;   // internal: the FP32-preconditioned run stopped improving
+
 struct RunResult {
   int status;
   int k;
@@ -268,8 +342,8 @@ double max_rel(const double* n2, const double* b2, int L, double* rel) {
 }
 
 // One run of preconditioned block BiCGGR from the current X (Sec. 2, algorithm box).
-int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, double tol, int maxit,
-                double div_thresh, const double* b2, bbicggr_opts* o, int* hist_n,
+int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precision, double tol,
+                int maxit, double div_thresh, const double* b2, bbicggr_opts* o, int* hist_n,
                 long long* hop_count, RunResult* out, cudaStream_t s) {
   const Op& op = c->op;
   const long long rows = (long long)op.g.V * 12;
@@ -303,7 +377,7 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, double tol,
 
   // F_0 = M R_0;  V_0 = W_0 = A F_0
   double* res;
-  CHECK(precondition(c, R, pF, pT, &res, L, j, hop_count, s));
+  CHECK(precondition(c, R, pF, pT, &res, L, j, precision, hop_count, s));
   if (res != pF) { pT = pF; pF = res; }
   LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pF, W, L, s));
   ++*hop_count;
@@ -312,11 +386,14 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, double tol,
   LAUNCH(WD_K_GRAM, 2, launch_gram(Rt, V, L, rows, part, st, GRAM_RTV, false, s));
 
   int k = 0;
+  double best = m;
+  int k_best = 0;
+  const int stall = precision == 1 ? o->stall_window : 0;
   for (;;) {
     if (k >= maxit) { out->status = WD_NOT_CONVERGED; break; }
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_alpha(st, L, s));                       // alpha_k, zeta_k
     LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(P, V, U, L, rows, st, s));           // U_k = (P_k - zeta_k V_k) alpha_k
-    CHECK(precondition(c, U, pG, pT, &res, L, j, hop_count, s));   // G_k = M U_k
+    CHECK(precondition(c, U, pG, pT, &res, L, j, precision, hop_count, s));   // G_k = M U_k
     if (res != pG) { pT = pG; pG = res; }
     LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pG, Y, L, s));                  // Y_k = A G_k
     ++*hop_count;
@@ -329,7 +406,9 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, double tol,
     if (!std::isfinite(m)) { out->status = WD_BREAKDOWN; break; }
     if (m <= tol) { out->status = WD_OK; break; }
     if (m > div_thresh) { out->status = WD_DIVERGED; break; }
-    CHECK(precondition(c, R, pF, pT, &res, L, j, hop_count, s));   // F_{k+1} = M R_{k+1}
+    if (m < best) { best = m; k_best = k; }
+    if (stall > 0 && k - k_best >= stall) { out->status = RUN_STALLED; break; }
+    CHECK(precondition(c, R, pF, pT, &res, L, j, precision, hop_count, s));   // F_{k+1} = M R_{k+1}
     if (res != pF) { pT = pF; pF = res; }
     LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pF, W, L, s));                  // W_{k+1} = A F_{k+1}
     ++*hop_count;
@@ -341,11 +420,6 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, double tol,
   return WD_OK;
 }
 
-// FP32 copies of links and clover inverse for the FP32 preconditioner.
-__global__ void to_float_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
-  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (float)a[i];
-}
 
 }  // namespace
 
@@ -368,6 +442,7 @@ void bbicggr_default_opts(bbicggr_opts* o) {
   o->precision = 0;
   o->history = nullptr;
   o->history_len = 0;
+  o->stall_window = 16;
 }
 
 const char* wd_strerror(int code) {
@@ -395,6 +470,8 @@ void wd_destroy(wd_ctx* c) {
   cudaFree(c->op.links32);
   cudaFree(c->op.clov_inv32);
   for (auto& b : c->blk) b.release();
+  for (auto& b : c->blk32) b.release();
+  for (int l = 0; l <= WD_LMAX; ++l) c->tile_r[l] = c->tile_block[l] = 0;
   c->part.release();
   c->stage_in.release();
   c->stage_out.release();
@@ -418,9 +495,7 @@ static int create_impl(wd_ctx* c, const void* links, const int dims[4], cudaStre
   CU(cudaMalloc(&flag, sizeof(int)));
   CU(cudaMemsetAsync(flag, 0, sizeof(int), s));
   CU(launch_clover_build(op, flag, s));
-  const size_t n = V * 4 * 18;
-  to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(op.links, op.links32, n);
-  CU(cudaGetLastError());
+  CU(launch_fp32_operator_copies(op, s));
   int h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -492,6 +567,26 @@ const char* wd_profile_name(int cls) {
   return (cls >= 0 && cls < WD_K_COUNT) ? names[cls] : "unknown";
 }
 
+int wd_set_tile(wd_ctx* c, int L, int rhs_per_thread, int block) {
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  CHECK(check_L(L));
+  if ((rhs_per_thread != 1 && rhs_per_thread != 2) || L % rhs_per_thread != 0 ||
+      (block != 64 && block != 128 && block != 256)) {
+    set_err("tile (%d RHS/thread, %d threads) not available for L = %d", rhs_per_thread, block, L);
+    return WD_EINVAL;
+  }
+  c->tile_r[L] = rhs_per_thread;
+  c->tile_block[L] = block;
+  return WD_OK;
+}
+
+int wd_tuned_tile(const wd_ctx* c, int L, int* rhs_per_thread, int* block) {
+  if (!c || L < 1 || L > WD_LMAX || !c->tile_r[L]) { set_err("no tuned tile for this L"); return WD_EINVAL; }
+  if (rhs_per_thread) *rhs_per_thread = c->tile_r[L];
+  if (block) *block = c->tile_block[L];
+  return WD_OK;
+}
+
 int wd_query(const wd_ctx* c, int dims[4], long long* volume, double* kappa, double* csw) {
   if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
   if (dims) for (int m = 0; m < 4; ++m) dims[m] = c->op.g.d[m];
@@ -527,7 +622,7 @@ int jacobi_precond(wd_ctx* c, const void* R, void* G, int L, int j, int precisio
   CHECK(check_ptr(R, "R"));
   CHECK(check_ptr(G, "G"));
   if (j < 0) { set_err("j = %d < 0", j); return WD_EINVAL; }
-  if (precision != 0) { set_err("precision %d not available", precision); return WD_EINVAL; }
+  if (precision != 0 && precision != 1) { set_err("precision %d not in {0, 1}", precision); return WD_EINVAL; }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = block_bytes(c, L);
   const double* rd;
@@ -544,7 +639,8 @@ int jacobi_precond(wd_ctx* c, const void* R, void* G, int L, int j, int precisio
   // first buffer when j is odd.
   double* first = (j % 2 == 1) ? gd : tmp;
   double* second = (j % 2 == 1) ? tmp : gd;
-  CHECK(precondition(c, rd, first, second, &res, L, j, nullptr, s));
+  if (precision == 1) { first = gd; second = tmp; }   // the FP32 sweeps always finish in `first`
+  CHECK(precondition(c, rd, first, second, &res, L, j, precision, nullptr, s));
   if (res != gd) LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(gd, res, bytes, cudaMemcpyDeviceToDevice, s));
   if (!g_dev) CU(cudaMemcpyAsync(G, gd, bytes, cudaMemcpyDeviceToHost, s));
   if (staged_r || !g_dev) CU(cudaStreamSynchronize(s));
@@ -564,11 +660,11 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
   bbicggr_opts o;
   bbicggr_default_opts(&o);
   if (opts) o = *opts;
-  if (o.maxit < 0 || o.max_restarts < 0 || !(o.div_thresh > 0.0)) {
+  if (o.maxit < 0 || o.max_restarts < 0 || !(o.div_thresh > 0.0) || o.stall_window < 0) {
     set_err("invalid options");
     return WD_EINVAL;
   }
-  if (o.precision != 0) { set_err("precision %d not available", o.precision); return WD_EINVAL; }
+  if (o.precision != 0 && o.precision != 1) { set_err("precision %d not in {0, 1}", o.precision); return WD_EINVAL; }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CHECK(ensure_workspace(c, L));
   const size_t bytes = block_bytes(c, L);
@@ -595,18 +691,34 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
       return WD_EINVAL;
     }
 
-  int status = WD_OK, iters = 0, restarts = 0, hist_n = 0;
+  int status = WD_OK, iters = 0, restarts = 0, hist_n = 0, fallbacks = 0;
+  int prec = o.precision;
+  const bool may_fall_back = prec == 1 && o.stall_window > 0;
+  if (may_fall_back)   // keep X_0 for a restart with the FP64 preconditioner
+    LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(c->blk[B_X0].d(), Xd, bytes, cudaMemcpyDeviceToDevice, s));
   long long mvm_paper = 0, hops = 0;
   RunResult rr{};
   double true_rel[WD_LMAX];
   double mtrue = 0.0;
   for (;;) {
     long long hop_run = 0;
-    CHECK(run_bbicggr(c, Bd, Xd, L, j, tol, o.maxit - iters, o.div_thresh, b2, &o, &hist_n,
+    CHECK(run_bbicggr(c, Bd, Xd, L, j, prec, tol, o.maxit - iters, o.div_thresh, b2, &o, &hist_n,
                       &hop_run, &rr, s));
     iters += rr.k;
     hops += hop_run;
     mvm_paper += (long long)L * (2LL * (j + 1) * rr.k + 1);
+    if (prec == 1 && may_fall_back &&
+        (rr.status == RUN_STALLED || rr.status == WD_BREAKDOWN || rr.status == WD_DIVERGED) &&
+        iters < o.maxit) {
+      // Start over from X_0 with the FP64 preconditioner.  Restarting from the stalled iterate is
+      // not used: near the critical kappa its residual lies in the operator's low-mode space, from
+      // which block BiCGGR (with R~_0 = R_0 or the original R~_0) itself fails to converge.
+      LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(Xd, c->blk[B_X0].d(), bytes, cudaMemcpyDeviceToDevice, s));
+      prec = 0;
+      ++fallbacks;
+      continue;
+    }
+    if (rr.status == RUN_STALLED) rr.status = WD_NOT_CONVERGED;
     // true residual ||b_i - A x_i|| / ||b_i||
     double* T = c->blk[B_T].d();
     LAUNCH(WD_K_RESID, 1, launch_resid_f64(c->op, Xd, Bd, T, L, s));
@@ -639,6 +751,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     if (info->rec_resid) std::memcpy(info->rec_resid, rr.rec, L * sizeof(double));
     if (info->true_resid) std::memcpy(info->true_resid, true_rel, L * sizeof(double));
     info->history_count = hist_n;
+    info->fallbacks = fallbacks;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   harvest(c);

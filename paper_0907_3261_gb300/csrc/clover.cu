@@ -123,8 +123,8 @@ __device__ void pack_herm6(const Cx<double> m[6][6], double* out) {
 }
 
 __global__ void clover_build_kernel(const double* __restrict__ links, double* __restrict__ clov,
-                                    double* __restrict__ clov_inv, float* __restrict__ clov_inv32,
-                                    Geom g, double kappa, double csw, int* singular) {
+                                    double* __restrict__ clov_inv, Geom g, double kappa,
+                                    double csw, int* singular) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   // F_{mu nu} for (x,y) (x,z) (x,t) (y,z) (y,t) (z,t)
@@ -155,8 +155,6 @@ __global__ void clover_build_kernel(const double* __restrict__ links, double* __
     if (!invert6(blk, inv)) atomicExch(singular, 1);
     double* oi = clov_inv + ((size_t)s * 2 + ch) * CLOV_REALS;
     pack_herm6(inv, oi);
-    if (clov_inv32)
-      for (int i = 0; i < CLOV_REALS; ++i) clov_inv32[((size_t)s * 2 + ch) * CLOV_REALS + i] = (float)oi[i];
   }
 }
 
@@ -165,6 +163,6 @@ __global__ void clover_build_kernel(const double* __restrict__ links, double* __
 cudaError_t launch_clover_build(const Op& op, int* singular_dev, cudaStream_t st) {
   const int threads = 64;
   clover_build_kernel<<<(op.g.V + threads - 1) / threads, threads, 0, st>>>(
-      op.links, op.clov, op.clov_inv, op.clov_inv32, op.g, op.kappa, op.csw, singular_dev);
+      op.links, op.clov, op.clov_inv, op.g, op.kappa, op.csw, singular_dev);
   return cudaGetLastError();
 }

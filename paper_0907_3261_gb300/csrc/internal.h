@@ -17,8 +17,8 @@ struct Op {
   double* links;     // [V][4][3][3] complex
   double* clov;      // [V][2][36]  A_D blocks, packed Hermitian
   double* clov_inv;  // [V][2][36]  A_D^{-1} blocks
-  float* links32;
-  float* clov_inv32;
+  float* links32;     // [4 mu][9 entries][V] complex, FP32 (component-major)
+  float* clov_inv32;  // [2 chirality][36][V], FP32 (component-major)
 };
 
 // ---- dslash.cu (FP64)
@@ -28,6 +28,18 @@ cudaError_t launch_resid_f64(const Op& op, const double* x, const double* b, dou
 cudaError_t launch_jacobi_f64(const Op& op, const double* g_in, const double* u, double* g_out,
                               int L, cudaStream_t st);
 cudaError_t launch_site_inverse_f64(const Op& op, const double* u, double* g_out, int L,
+                                    cudaStream_t st);
+
+// ---- dslash.cu: the FP32 preconditioner.  Its blocks (u32, g32) are component-major,
+// [spin*3+colour][site][rhs]; FP64 blocks are site-major.  Exactly one of g32 / g64 is non-null.
+cudaError_t launch_fp32_operator_copies(const Op& op, cudaStream_t st);
+cudaError_t launch_site_inverse_mixed(const Op& op, const double* u, float* u32, float* g32,
+                                      double* g64, int L, cudaStream_t st);
+
+// FP32 sweep with `rhs_per_thread` (1 or 2; divides L) RHS per thread and `block` threads (64,
+// 128, 256) per CTA; exactly one of g32 / g64 is non-null.
+cudaError_t launch_jacobi_f32_tiled(const Op& op, const float* g_in, const float* u32, float* g32,
+                                    double* g64, int L, int rhs_per_thread, int block,
                                     cudaStream_t st);
 
 // ---- clover.cu

@@ -29,6 +29,7 @@ def test_host_only_entry_points(lib):
     o = lib.Opts()
     L.bbicggr_default_opts(ctypes.byref(o))
     assert o.maxit == 10000 and o.div_thresh == 1e2 and o.max_restarts == 3 and o.precision == 0
+    assert o.stall_window == 16
 
 
 def test_argument_errors_need_no_gpu(lib):

@@ -13,6 +13,11 @@ pytestmark = pytest.mark.gpu
 APPLY_TOL = 1e-12     # relative, wd_apply vs oracle
 SOLVE_X_TOL = 1e-9    # ||X - X_oracle|| / ||X||
 TRUE_RES_TOL = 1e-12  # per column
+# FP32 Jacobi sweeps: each sweep sums ~100 FP32 products per component (8 hops x 2 x 3 colour
+# terms, the 6x6 inverse block); with unit roundoff 2^-24 = 6e-8 the worst-case relative error of a
+# sweep is ~100 x 6e-8 = 6e-6, and later sweeps carry earlier errors forward contracted by the
+# Jacobi iteration matrix.  1e-5 bounds j <= 12 sweeps at the kappa values tested.
+MIXED_TOL = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -231,6 +236,96 @@ def test_full_size_16_16_16_32(wd):
     assert rel(Y, Y_ref) <= APPLY_TOL
     del Y, Y_ref
     B = I.z4_noise(dims, 12, seed=1)
-    Xg, info = wd.bbicggr_solve(ctx, dev(B), j=12, tol=1e-12)
+    for precision in (0, 1):
+        Xg, info = wd.bbicggr_solve(ctx, dev(B), j=12, tol=1e-12, precision=precision)
+        assert info["status"] == wd.WD_OK
+        assert S.true_residual(op, B, host(Xg)).max() <= TRUE_RES_TOL
+
+
+# ---------------------------------------------------------------- FP32 preconditioner (precision 1)
+@pytest.mark.parametrize("j", [1, 2, 5, 12])
+@pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 4), ((3, 4, 5, 6), 7), ((8, 8, 8, 16), 12)])
+def test_jacobi_fp32_matches_oracle(wd, j, dims, L):
+    links = I.random_links(dims, 0.3, seed=2)
+    op = O.WilsonClover(links, dims, 0.12, 1.0)
+    R = I.gaussian_block(dims, L, seed=5)
+    ctx = wd.wd_create(dev(links), dims, 0.12, 1.0)
+    G = host(wd.jacobi_precond(ctx, dev(R), j, precision=1))
+    G_ref = S.jacobi(op, R, j)
+    assert rel(G, G_ref) <= MIXED_TOL
+    assert max_elem_rel(G, G_ref) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("B_kind,L,j", [("point", 4, 4), ("z4", 12, 4), ("z4", 3, 1)])
+def test_mixed_solve_matches_fp64_oracle(wd, B_kind, L, j):
+    """An FP32 preconditioner changes M, not what block BiCGGR computes: the FP64 outer
+    recurrences still reach the FP64 solution."""
+    dims = (4, 4, 4, 4)
+    links = I.random_links(dims, 0.3, seed=0)
+    op = O.WilsonClover(links, dims, 0.115, 1.0)
+    B = I.point_sources(dims, L) if B_kind == "point" else I.z4_noise(dims, L, seed=1)
+    ref = S.solve(op, B, j=j, tol=1e-12)
+    ctx = wd.wd_create(dev(links), dims, 0.115, 1.0)
+    Xg, info = wd.bbicggr_solve(ctx, dev(B), j=j, tol=1e-12, precision=1)
+    Xg = host(Xg)
     assert info["status"] == wd.WD_OK
-    assert S.true_residual(op, B, host(Xg)).max() <= TRUE_RES_TOL
+    assert S.true_residual(op, B, Xg).max() <= TRUE_RES_TOL
+    assert rel(Xg, ref.X) <= SOLVE_X_TOL
+    assert abs(info["iters"] - ref.iters) <= max(2, ref.iters // 10)
+
+
+def test_mixed_solve_8_8_8_16_near_critical(wd):
+    dims = (8, 8, 8, 16)
+    links = I.random_links(dims, 0.2, seed=0)
+    op = O.WilsonClover(links, dims, 0.132, 1.0)
+    B = I.z4_noise(dims, 12, seed=1)
+    ctx = wd.wd_create(dev(links), dims, 0.132, 1.0)
+    X64, i64 = wd.bbicggr_solve(ctx, dev(B), j=12, tol=1e-12)
+    X32, i32 = wd.bbicggr_solve(ctx, dev(B), j=12, tol=1e-12, precision=1)
+    assert i64["status"] == i32["status"] == wd.WD_OK
+    assert S.true_residual(op, B, host(X32)).max() <= TRUE_RES_TOL
+    assert rel(host(X32), host(X64)) <= SOLVE_X_TOL
+
+
+def test_mixed_solve_falls_back_to_fp64_preconditioner_near_critical(wd):
+    """Near the critical kappa the rounding of an FP32 preconditioner (a non-linear M) can stall
+    block BiCGGR, which needs a fixed linear M; the solve then continues from X with the FP64
+    preconditioner and still reaches the FP64 answer."""
+    dims = (6, 6, 6, 6)
+    links = I.random_links(dims, 0.2, seed=0)
+    op = O.WilsonClover(links, dims, 0.134, 1.0)
+    B = I.z4_noise(dims, 4, seed=1)
+    ctx = wd.wd_create(dev(links), dims, 0.134, 1.0)
+    X64, i64 = wd.bbicggr_solve(ctx, dev(B), j=4, tol=1e-12, maxit=2000)
+    X32, i32 = wd.bbicggr_solve(ctx, dev(B), j=4, tol=1e-12, precision=1, maxit=2000)
+    assert i64["status"] == i32["status"] == wd.WD_OK
+    assert S.true_residual(op, B, host(X32)).max() <= TRUE_RES_TOL
+    assert rel(host(X32), host(X64)) <= SOLVE_X_TOL
+    assert i32["fallbacks"] in (0, 1)
+    _, i0 = wd.bbicggr_solve(ctx, dev(B), j=4, tol=1e-12, precision=1, maxit=300, stall_window=0)
+    assert i0["fallbacks"] == 0
+
+
+@pytest.mark.parametrize("tile", [(1, 64), (1, 128), (1, 256), (2, 64), (2, 128), (2, 256)])
+def test_fp32_sweep_tiles_match_oracle(wd, tile):
+    """Every tile the autotuner may pick computes the same sweep."""
+    dims, L = (3, 4, 5, 6), 6
+    links = I.random_links(dims, 0.4, seed=2)
+    op = O.WilsonClover(links, dims, 0.12, 1.0)
+    R = I.gaussian_block(dims, L, seed=5)
+    ctx = wd.wd_create(dev(links), dims, 0.12, 1.0)
+    wd.wd_set_tile(ctx, L, *tile)
+    G = host(wd.jacobi_precond(ctx, dev(R), 5, precision=1))
+    assert wd.wd_tuned_tile(ctx, L) == tile
+    assert rel(G, S.jacobi(op, R, 5)) <= MIXED_TOL
+
+
+def test_autotuner_picks_a_valid_tile(wd):
+    dims, L = (4, 4, 4, 8), 12
+    ctx = wd.wd_create(dev(I.random_links(dims, 0.3, seed=0)), dims, 0.12, 1.0)
+    assert wd.wd_tuned_tile(ctx, L) is None
+    wd.jacobi_precond(ctx, dev(I.z4_noise(dims, L, seed=1)), 4, precision=1)
+    r, b = wd.wd_tuned_tile(ctx, L)
+    assert r in (1, 2) and L % r == 0 and b in (64, 128, 256)
+    with pytest.raises(wd.WDError):
+        wd.wd_set_tile(ctx, 3, 2, 128)          # 2 does not divide L = 3
