@@ -59,6 +59,21 @@ def algorithmic_bytes(kind: str, L: int, real_bytes: int = 8) -> int:
     raise ValueError(kind)
 
 
+def source_seed(rank: int) -> int:
+    """Each rank solves its own independent sources."""
+    return 1 + rank
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Largest value over all ranks (timings); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -246,7 +261,7 @@ def main():
     prec = {"fp64": 0, "mixed": 1}[args.precision]
 
     links = torch.from_numpy(I.random_links(DIMS, LINK_EPS, seed=0)).to(dev)
-    Bh = torch.from_numpy(I.z4_noise(DIMS, L_RHS, seed=1 + rank)).pin_memory()
+    Bh = torch.from_numpy(I.z4_noise(DIMS, L_RHS, seed=source_seed(rank))).pin_memory()
     B = Bh.to(dev)
     ctx = wd.wd_create(links, DIMS, KAPPA, CSW)
     X = torch.zeros_like(B)
@@ -262,11 +277,7 @@ def main():
             f"{info['seconds']:.3f}s true={info['max_true_resid']:.2e}")
 
     def maxr(v: float) -> float:
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(v, dist, dev)
 
     # ---- device-timed region: inputs resident in HBM
     wd.wd_profile_reset(ctx)
