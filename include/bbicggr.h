@@ -55,6 +55,7 @@ enum {
 #define WD_LMAX 16        /* largest number of right-hand sides per solve */
 
 typedef struct wd_ctx wd_ctx;   /* opaque; owned by the library */
+typedef struct wd_net wd_net;   /* opaque learned preconditioner; owned by the library */
 
 /* Solver options.  Fill with bbicggr_default_opts() and change what you need. */
 typedef struct {
@@ -73,6 +74,9 @@ typedef struct {
                              preconditioner (block BiCGGR needs a fixed linear M, and FP32
                              rounding of M can stall it near the critical kappa).  Default 16;
                              0 disables the fallback.  Costs one more N x L block of workspace */
+  wd_net* net;            /* not NULL: M is this learned network (FP32) instead of j-step Jacobi;
+                             the stall rule above applies and its fallback is FP64 Jacobi with the
+                             solve's j.  mvm_paper then counts the products with A only */
 } bbicggr_opts;
 
 /* Solve report.  rec_resid and true_resid, when not NULL, are caller-owned host arrays of L. */
@@ -142,6 +146,30 @@ void bbicggr_default_opts(bbicggr_opts* opts);
 const char* wd_strerror(int code);
 const char* wd_last_error(void);
 
+/* ---- Learned preconditioner (the paper's future work on a better preconditioner, Sec. 4).
+ * A network of `layers` gauge-covariant layers, linear in the spinor, channels
+ * 1 -> hidden -> ... -> hidden -> 1 (hidden 1, 2 or 4):
+ *   out_{c'}(x) = sum_{d=0..8} sum_c W[d][c'][c] (T_d psi_c)(x),   T_0 = 1,
+ *   (T_{1+mu} psi)(x) = U_mu(x) psi(x+mu),  (T_{5+mu} psi)(x) = U_mu(x-mu)^H psi(x-mu),
+ * W[d][c'][c] a complex 4x4 spin matrix.  Weights at the ABI: complex128, per layer
+ * [9][C_out][C_in][4][4], layers concatenated (wd_net_num_weights complex numbers); stored as
+ * complex64.  Activations FP32.  Training: loss = (1/L) sum_i ||N(r_i) - e_i||^2 / ||e_i||^2 over
+ * pairs (r_i, e_i = A^{-1} r_i), gradient d loss / d conj(W), Adam on (Re W, Im W). */
+int wd_net_create(wd_net** out, int layers, int hidden, const void* weights /* host or device */);
+void wd_net_destroy(wd_net* net);
+long long wd_net_num_weights(const wd_net* net);
+int wd_net_set_weights(wd_net* net, const void* weights);   /* also resets the Adam state */
+int wd_net_get_weights(const wd_net* net, void* out);       /* host or device, complex128 */
+/* G = N(R) for device blocks R, G (N x L, complex128, site-major). */
+int wd_net_apply(wd_ctx* ctx, wd_net* net, const void* R, void* G, int L, void* stream);
+/* Forward and backward pass on device blocks R, E: *loss (host, may be NULL) and the gradient
+ * d loss / d conj(W), kept in the network for wd_net_adam_step and copied to `grad` (complex128,
+ * host or device, may be NULL).  Synchronises the stream. */
+int wd_net_loss_grad(wd_ctx* ctx, wd_net* net, const void* R, const void* E, int L, double* loss,
+                     void* grad, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the gradient of the last loss_grad. */
+int wd_net_adam_step(wd_net* net, double lr, void* stream);
+
 /* Per-kernel instrumentation.  Every kernel launch of a context is counted per kernel class
  * (WD_K_*).  With timing on, each launch is also bracketed by two CUDA events recorded on the
  * launching stream, and the elapsed device times are summed when the call that launched them
@@ -161,6 +189,7 @@ enum {
   WD_K_COLNORM,        /* column norms */
   WD_K_COPY,           /* device-to-device block copies */
   WD_K_CONVERT,        /* FP64 <-> FP32 conversions of the FP32 preconditioner */
+  WD_K_NET,            /* learned preconditioner G = N(R) (all its kernels) */
   WD_K_COUNT
 };
 int wd_profile_enable(wd_ctx* ctx, int timing_on);

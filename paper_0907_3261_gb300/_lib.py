@@ -32,7 +32,7 @@ class WDError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("maxit", C.c_int), ("div_thresh", C.c_double), ("max_restarts", C.c_int),
                 ("precision", C.c_int), ("history", C.POINTER(C.c_double)),
-                ("history_len", C.c_int), ("stall_window", C.c_int)]
+                ("history_len", C.c_int), ("stall_window", C.c_int), ("net", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -78,6 +78,19 @@ def lib():
     L.wd_last_error.restype = C.c_char_p
     L.wd_query.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(d),
                            C.POINTER(d)]
+    L.wd_net_create.argtypes = [C.POINTER(vp), i, i, vp]
+    L.wd_net_destroy.argtypes = [vp]
+    L.wd_net_destroy.restype = None
+    L.wd_net_num_weights.argtypes = [vp]
+    L.wd_net_num_weights.restype = C.c_longlong
+    L.wd_net_set_weights.argtypes = [vp, vp]
+    L.wd_net_get_weights.argtypes = [vp, vp]
+    L.wd_net_apply.argtypes = [vp, vp, vp, vp, i, vp]
+    L.wd_net_loss_grad.argtypes = [vp, vp, vp, vp, i, C.POINTER(d), vp, vp]
+    L.wd_net_adam_step.argtypes = [vp, d, vp]
+    for name in ("wd_net_create", "wd_net_set_weights", "wd_net_get_weights", "wd_net_apply",
+                 "wd_net_loss_grad", "wd_net_adam_step"):
+        getattr(L, name).restype = C.c_int
     L.wd_profile_enable.argtypes = [vp, i]
     L.wd_profile_reset.argtypes = [vp]
     L.wd_profile_read.argtypes = [vp, i, C.POINTER(C.c_longlong), C.POINTER(d)]
@@ -214,7 +227,7 @@ def jacobi_precond_noalloc(ctx: Context, R, G, j: int, stream=None):
 
 def bbicggr_solve(ctx: Context, B, X=None, j: int = 12, tol: float = 1e-12, maxit: int = 10000,
                   div_thresh: float = 1e2, max_restarts: int = 3, precision: int = 0,
-                  history: int = 0, stall_window: int = 16, stream=None):
+                  history: int = 0, stall_window: int = 16, net=None, stream=None):
     """Solve A X = B by preconditioned block BiCGGR.  Returns (X, info dict).
 
     ``X`` (if given) holds X_0 and receives the solution; by default X_0 = 0.  Solver outcomes
@@ -233,6 +246,8 @@ def bbicggr_solve(ctx: Context, B, X=None, j: int = 12, tol: float = 1e-12, maxi
     o.maxit, o.div_thresh, o.max_restarts, o.precision = int(maxit), float(div_thresh), \
         int(max_restarts), int(precision)
     o.stall_window = int(stall_window)
+    if net is not None:
+        o.net = net.handle
     hist = (C.c_double * max(history, 1))()
     if history:
         o.history = C.cast(hist, C.POINTER(C.c_double))
@@ -255,7 +270,7 @@ def bbicggr_solve(ctx: Context, B, X=None, j: int = 12, tol: float = 1e-12, maxi
     return X, out
 
 
-WD_K_COUNT = 13
+WD_K_COUNT = 14
 
 
 def wd_profile_enable(ctx: Context, timing_on: bool = True) -> None:
@@ -289,3 +304,96 @@ def wd_tuned_tile(ctx: Context, L: int):
 def wd_set_tile(ctx: Context, L: int, rhs_per_thread: int, block: int) -> None:
     """Fix the FP32 sweep's tile for this L instead of autotuning it."""
     _check(lib().wd_set_tile(ctx.handle, int(L), int(rhs_per_thread), int(block)))
+
+
+
+# ---------------------------------------------------------------- learned preconditioner
+class Net:
+    """Owns a wd_net*: weights, Adam state and workspace of one preconditioner network."""
+
+    def __init__(self, handle: int, layers: int, hidden: int):
+        self.handle = C.c_void_p(handle)
+        self.layers = layers
+        self.hidden = hidden
+        self.channels = [1] + [hidden] * (layers - 1) + [1]
+
+    def shapes(self):
+        ch = self.channels
+        return [(9, ch[i + 1], ch[i], 4, 4) for i in range(self.layers)]
+
+    def close(self):
+        if self.handle and self.handle.value:
+            lib().wd_net_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _flat_weights(weights):
+    return np.ascontiguousarray(np.concatenate([np.asarray(w, np.complex128).ravel()
+                                                for w in weights]))
+
+
+def wd_net_create(layers: int, hidden: int, weights) -> Net:
+    """Network with the given initial weights (list of [9][C_out][C_in][4][4] arrays)."""
+    flat = _flat_weights(weights)
+    out = C.c_void_p()
+    _check(lib().wd_net_create(C.byref(out), int(layers), int(hidden), C.c_void_p(flat.ctypes.data)))
+    net = Net(out.value, layers, hidden)
+    if lib().wd_net_num_weights(net.handle) != flat.size:
+        raise ValueError("weights do not match the architecture")
+    return net
+
+
+def wd_net_destroy(net: Net) -> None:
+    net.close()
+
+
+def _unflatten(net: Net, flat):
+    out, off = [], 0
+    for shp in net.shapes():
+        n = int(np.prod(shp))
+        out.append(flat[off:off + n].reshape(shp))
+        off += n
+    return out
+
+
+def wd_net_get_weights(net: Net):
+    flat = np.empty(lib().wd_net_num_weights(net.handle), dtype=np.complex128)
+    _check(lib().wd_net_get_weights(net.handle, C.c_void_p(flat.ctypes.data)))
+    return _unflatten(net, flat)
+
+
+def wd_net_set_weights(net: Net, weights) -> None:
+    flat = _flat_weights(weights)
+    _check(lib().wd_net_set_weights(net.handle, C.c_void_p(flat.ctypes.data)))
+
+
+def wd_net_apply(ctx: Context, net: Net, R, G=None, stream=None):
+    """G = N(R) for device (torch) blocks."""
+    pr, L, kr = _ptr_and_L(R, "R")
+    if G is None:
+        G = _empty_like(R)
+    pg, _, kg = _ptr_and_L(G, "G")
+    _check(lib().wd_net_apply(ctx.handle, net.handle, pr, pg, L, _stream(stream)))
+    return G
+
+
+def wd_net_loss_grad(ctx: Context, net: Net, R, E, want_grad: bool = True, stream=None):
+    """(loss, gradient d loss / d conj(W) as a list of arrays or None) for device blocks R, E."""
+    pr, L, kr = _ptr_and_L(R, "R")
+    pe, _, ke = _ptr_and_L(E, "E")
+    loss = C.c_double()
+    flat = np.empty(lib().wd_net_num_weights(net.handle), dtype=np.complex128) if want_grad else None
+    _check(lib().wd_net_loss_grad(ctx.handle, net.handle, pr, pe, L, C.byref(loss),
+                                  C.c_void_p(flat.ctypes.data) if want_grad else None,
+                                  _stream(stream)))
+    return float(loss.value), (_unflatten(net, flat) if want_grad else None)
+
+
+def wd_net_adam_step(net: Net, lr: float, stream=None) -> None:
+    _check(lib().wd_net_adam_step(net.handle, float(lr), _stream(stream)))

@@ -119,6 +119,7 @@ struct wd_ctx {
   // autotuned tile of the FP32 sweep per L: RHS per thread and threads per CTA (0 = not tuned)
   int tile_r[WD_LMAX + 1] = {};
   int tile_block[WD_LMAX + 1] = {};
+  wd_net* active_net = nullptr;   // learned preconditioner of the running solve (mode 2)
 };
 
 namespace {
@@ -272,9 +273,15 @@ int stage_input(const void* p, size_t bytes, DevBuf& stage, const double** out, 
 int precondition(wd_ctx* c, const double* R, double* a, double* b, double** res, int L, int j,
                  int precision, long long* hop_count, cudaStream_t s) {
   const Op& op = c->op;
-  if (j == 0) {
+  if (j == 0 && precision != 2) {
     LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(a, R, block_bytes(c, L), cudaMemcpyDeviceToDevice, s));
     *res = a;
+    return WD_OK;
+  }
+  if (precision == 2) {   // learned network
+    *res = a;
+    Timed timed_(c, WD_K_NET, 0, s);
+    CHECK(wd_net_precondition(c, c->active_net, R, a, L, s));
     return WD_OK;
   }
   if (precision == 1) {
@@ -388,7 +395,7 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
   int k = 0;
   double best = m;
   int k_best = 0;
-  const int stall = precision == 1 ? o->stall_window : 0;
+  const int stall = precision != 0 ? o->stall_window : 0;
   for (;;) {
     if (k >= maxit) { out->status = WD_NOT_CONVERGED; break; }
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_alpha(st, L, s));                       // alpha_k, zeta_k
@@ -443,6 +450,7 @@ void bbicggr_default_opts(bbicggr_opts* o) {
   o->history = nullptr;
   o->history_len = 0;
   o->stall_window = 16;
+  o->net = nullptr;
 }
 
 const char* wd_strerror(int code) {
@@ -563,7 +571,7 @@ int wd_profile_read(const wd_ctx* c, int cls, long long* launches, double* ms) {
 const char* wd_profile_name(int cls) {
   static const char* names[WD_K_COUNT] = {
       "dslash_apply", "dslash_resid", "dslash_jacobi", "site_inverse", "update_u", "update_xr",
-      "update_pv", "gram", "trace", "solve_ll", "colnorm", "copy", "convert"};
+      "update_pv", "gram", "trace", "solve_ll", "colnorm", "copy", "convert", "net"};
   return (cls >= 0 && cls < WD_K_COUNT) ? names[cls] : "unknown";
 }
 
@@ -692,8 +700,9 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     }
 
   int status = WD_OK, iters = 0, restarts = 0, hist_n = 0, fallbacks = 0;
-  int prec = o.precision;
-  const bool may_fall_back = prec == 1 && o.stall_window > 0;
+  int prec = o.net ? 2 : o.precision;
+  c->active_net = o.net;
+  const bool may_fall_back = prec != 0 && o.stall_window > 0;
   if (may_fall_back)   // keep X_0 for a restart with the FP64 preconditioner
     LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(c->blk[B_X0].d(), Xd, bytes, cudaMemcpyDeviceToDevice, s));
   long long mvm_paper = 0, hops = 0;
@@ -706,8 +715,8 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
                       &hop_run, &rr, s));
     iters += rr.k;
     hops += hop_run;
-    mvm_paper += (long long)L * (2LL * (j + 1) * rr.k + 1);
-    if (prec == 1 && may_fall_back &&
+    mvm_paper += (long long)L * (2LL * ((prec == 2 ? 0 : j) + 1) * rr.k + 1);
+    if (prec != 0 && may_fall_back &&
         (rr.status == RUN_STALLED || rr.status == WD_BREAKDOWN || rr.status == WD_DIVERGED) &&
         iters < o.maxit) {
       // Start over from X_0 with the FP64 preconditioner.  Restarting from the stalled iterate is

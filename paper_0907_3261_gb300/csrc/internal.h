@@ -89,3 +89,22 @@ cudaError_t launch_update_pv(double* P, double* V, const double* R, const double
 struct wd_ctx;
 const Op* wd_ctx_op(const wd_ctx* ctx);
 void wd_set_error(const char* fmt, ...);
+
+// ---- net.cu: the learned preconditioner (activations FP32, component-major per channel)
+cudaError_t net_launch_layer(const Op& op, const float* in, float* out, const float2* W, int cin,
+                             int cout, int L, cudaStream_t st);
+cudaError_t net_launch_wgrad(const Op& op, const float* in, const float* delta, int cin, int cout,
+                             int L, double2* part, int nblocks, double2* grad, cudaStream_t st);
+cudaError_t net_launch_adjoint_weights(const float2* W, float2* Wa, int cin, int cout,
+                                       cudaStream_t st);
+cudaError_t net_launch_to_cm(const double* x, float* y, int V, int L, cudaStream_t st);
+cudaError_t net_launch_from_cm(const float* y, double* x, int V, int L, cudaStream_t st);
+cudaError_t net_launch_loss_delta(const float* y, const double* E, const double* wcol,
+                                  float* delta, double* part, int nblocks, double* loss, int V,
+                                  int L, cudaStream_t st);
+cudaError_t net_launch_adam(float2* W, const double2* G, float2* m, float2* v, int n, float lr,
+                            float b1, float b2, float eps, int t, cudaStream_t st);
+// ---- net_abi.cu
+struct wd_net;
+int wd_net_precondition(wd_ctx* ctx, wd_net* net, const double* R, double* G, int L,
+                        cudaStream_t s);

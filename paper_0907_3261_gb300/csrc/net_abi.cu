@@ -1,0 +1,278 @@
+// C-ABI of the learned preconditioner network (declared in include/bbicggr.h): weights, Adam
+// state and activation workspace of one network, inference G = N(R), and one training step on
+// pairs (R, E = A^{-1} R).  The kernels live in net.cu; see its header for the network.
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/bbicggr.h"
+#include "internal.h"
+
+namespace {
+
+bool dev_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+#define NCU(call)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      wd_set_error("%s failed: %s", #call, cudaGetErrorString(e_));                 \
+      return e_ == cudaErrorMemoryAllocation ? WD_ENOMEM : WD_ECUDA;                \
+    }                                                                               \
+  } while (0)
+#define NCHECK(rc)               \
+  do {                           \
+    int rc_ = (rc);              \
+    if (rc_ != WD_OK) return rc_; \
+  } while (0)
+
+constexpr int NET_MAX_LAYERS = 16;
+constexpr int NET_BLOCKS = 608;     // reduction blocks of the loss and weight-gradient kernels
+
+}  // namespace
+
+struct wd_net {
+  int layers = 0, hidden = 0;
+  std::vector<int> ch;          // channels: ch[0] = 1, ch[layers] = 1
+  std::vector<size_t> off;      // complex offset of each layer's weights
+  size_t nw = 0;                // complex weights in total
+  float2* W = nullptr;
+  float2* Wadj = nullptr;       // scratch for one layer's adjoint weights
+  double2* G = nullptr;         // d loss / d conj(W) of the last loss_grad call
+  float2* m = nullptr;
+  float2* v = nullptr;
+  int t = 0;                    // Adam steps taken
+  // workspace for (V, L)
+  long long V = 0;
+  int L = 0;
+  std::vector<float*> act;      // act[l]: input of layer l; act[layers]: output
+  float* dA = nullptr;
+  float* dB = nullptr;
+  double* wcol = nullptr;
+  double* loss = nullptr;
+  double* lpart = nullptr;
+  double2* wpart = nullptr;
+  double* norms = nullptr;
+  void free_ws() {
+    for (float* a : act) cudaFree(a);
+    act.clear();
+    cudaFree(dA); cudaFree(dB); cudaFree(wcol); cudaFree(loss); cudaFree(lpart); cudaFree(wpart);
+    cudaFree(norms);
+    dA = dB = nullptr; wcol = loss = lpart = norms = nullptr; wpart = nullptr;
+    V = 0; L = 0;
+  }
+};
+
+namespace {
+
+size_t chan_floats(long long V, int L) { return (size_t)12 * V * L * 2; }
+
+int net_workspace(wd_net* n, long long V, int L) {
+  if (n->V == V && n->L == L) return WD_OK;
+  n->free_ws();
+  const size_t cf = chan_floats(V, L) * sizeof(float);
+  n->act.assign(n->layers + 1, nullptr);
+  for (int l = 0; l <= n->layers; ++l) NCU(cudaMalloc(&n->act[l], cf * n->ch[l]));
+  int maxc = 1;
+  for (int c : n->ch) maxc = c > maxc ? c : maxc;
+  NCU(cudaMalloc(&n->dA, cf * maxc));
+  NCU(cudaMalloc(&n->dB, cf * maxc));
+  NCU(cudaMalloc(&n->wcol, WD_LMAX * sizeof(double)));
+  NCU(cudaMalloc(&n->loss, sizeof(double)));
+  NCU(cudaMalloc(&n->lpart, NET_BLOCKS * sizeof(double)));
+  NCU(cudaMalloc(&n->norms, (size_t)(PART_STRIDE * NET_BLOCKS + WD_LMAX) * sizeof(double2)));
+  size_t maxne = 0;
+  for (int l = 0; l < n->layers; ++l) {
+    const size_t ne = (size_t)9 * n->ch[l + 1] * n->ch[l] * 16;
+    maxne = ne > maxne ? ne : maxne;
+  }
+  NCU(cudaMalloc(&n->wpart, (size_t)NET_BLOCKS * maxne * sizeof(double2)));
+  n->V = V;
+  n->L = L;
+  return WD_OK;
+}
+
+// act[layers] = N(act[0]) (activations of every layer kept).
+int net_forward(const Op& op, wd_net* n, int L, cudaStream_t s) {
+  for (int l = 0; l < n->layers; ++l)
+    NCU(net_launch_layer(op, n->act[l], n->act[l + 1], n->W + n->off[l], n->ch[l], n->ch[l + 1], L, s));
+  return WD_OK;
+}
+
+__global__ void weights_from_c128(const double* in, float2* out, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2((float)in[2 * i], (float)in[2 * i + 1]);
+}
+__global__ void weights_to_c128(const float2* in, double* out, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) { out[2 * i] = in[i].x; out[2 * i + 1] = in[i].y; }
+}
+__global__ void wcol_kernel(const double* norm2, double* wcol, int L) {
+  const int i = threadIdx.x;
+  if (i < L) wcol[i] = 1.0 / ((double)L * norm2[i]);
+}
+
+int set_weights(wd_net* n, const void* w) {
+  double* tmp = nullptr;
+  const double* src = static_cast<const double*>(w);
+  if (!dev_ptr(w)) {
+    NCU(cudaMalloc(&tmp, n->nw * 16));
+    NCU(cudaMemcpy(tmp, w, n->nw * 16, cudaMemcpyHostToDevice));
+    src = tmp;
+  }
+  weights_from_c128<<<(unsigned)((n->nw + 255) / 256), 256>>>(src, n->W, n->nw);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(tmp);
+  NCU(e);
+  NCU(cudaMemset(n->m, 0, n->nw * sizeof(float2)));
+  NCU(cudaMemset(n->v, 0, n->nw * sizeof(float2)));
+  n->t = 0;
+  return WD_OK;
+}
+
+}  // namespace
+
+// Internal: G = N(R) for device blocks R, G (site-major FP64), used by the solver.
+int wd_net_precondition(wd_ctx* ctx, wd_net* n, const double* R, double* G, int L, cudaStream_t s) {
+  const Op& op = *wd_ctx_op(ctx);
+  NCHECK(net_workspace(n, op.g.V, L));
+  NCU(net_launch_to_cm(R, n->act[0], op.g.V, L, s));
+  NCHECK(net_forward(op, n, L, s));
+  NCU(net_launch_from_cm(n->act[n->layers], G, op.g.V, L, s));
+  return WD_OK;
+}
+
+extern "C" {
+
+int wd_net_create(wd_net** out, int layers, int hidden, const void* weights) {
+  if (!out) { wd_set_error("out is NULL"); return WD_EINVAL; }
+  *out = nullptr;
+  if (layers < 1 || layers > NET_MAX_LAYERS || (hidden != 1 && hidden != 2 && hidden != 4) ||
+      (layers == 1 && hidden != 1)) {
+    wd_set_error("network of %d layers x %d hidden channels not available (hidden 1, 2 or 4)",
+                 layers, hidden);
+    return WD_EINVAL;
+  }
+  if (!weights) { wd_set_error("weights is NULL"); return WD_EINVAL; }
+  wd_net* n = new (std::nothrow) wd_net();
+  if (!n) { wd_set_error("host allocation failed"); return WD_ENOMEM; }
+  n->layers = layers;
+  n->hidden = hidden;
+  n->ch.assign(layers + 1, hidden);
+  n->ch[0] = 1;
+  n->ch[layers] = 1;
+  for (int l = 0; l < layers; ++l) {
+    n->off.push_back(n->nw);
+    n->nw += (size_t)9 * n->ch[l + 1] * n->ch[l] * 16;
+  }
+  int rc = WD_OK;
+  if (cudaMalloc(&n->W, n->nw * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&n->Wadj, n->nw * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&n->G, n->nw * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&n->m, n->nw * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&n->v, n->nw * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    wd_set_error("device allocation for the network failed");
+    rc = WD_ENOMEM;
+  }
+  if (rc == WD_OK) rc = set_weights(n, weights);
+  if (rc != WD_OK) { wd_net_destroy(n); return rc; }
+  *out = n;
+  return WD_OK;
+}
+
+void wd_net_destroy(wd_net* n) {
+  if (!n) return;
+  n->free_ws();
+  cudaFree(n->W); cudaFree(n->Wadj); cudaFree(n->G); cudaFree(n->m); cudaFree(n->v);
+  delete n;
+}
+
+long long wd_net_num_weights(const wd_net* n) { return n ? (long long)n->nw : -1; }
+
+int wd_net_set_weights(wd_net* n, const void* weights) {
+  if (!n || !weights) { wd_set_error("net or weights is NULL"); return WD_EINVAL; }
+  return set_weights(n, weights);
+}
+
+int wd_net_get_weights(const wd_net* n, void* out) {
+  if (!n || !out) { wd_set_error("net or out is NULL"); return WD_EINVAL; }
+  double* tmp = nullptr;
+  NCU(cudaMalloc(&tmp, n->nw * 16));
+  weights_to_c128<<<(unsigned)((n->nw + 255) / 256), 256>>>(n->W, tmp, n->nw);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(out, tmp, n->nw * 16, cudaMemcpyDefault);
+  cudaFree(tmp);
+  NCU(e);
+  return WD_OK;
+}
+
+int wd_net_apply(wd_ctx* ctx, wd_net* n, const void* R, void* G, int L, void* stream) {
+  if (!ctx || !n || !R || !G) { wd_set_error("NULL argument"); return WD_EINVAL; }
+  if (L < 1 || L > WD_LMAX) { wd_set_error("L = %d outside [1, %d]", L, WD_LMAX); return WD_EINVAL; }
+  if (!dev_ptr(R) || !dev_ptr(G)) { wd_set_error("wd_net_apply takes device buffers"); return WD_EINVAL; }
+  return wd_net_precondition(ctx, n, static_cast<const double*>(R), static_cast<double*>(G), L,
+                             static_cast<cudaStream_t>(stream));
+}
+
+int wd_net_loss_grad(wd_ctx* ctx, wd_net* n, const void* R, const void* E, int L, double* loss,
+                     void* grad, void* stream) {
+  if (!ctx || !n || !R || !E) { wd_set_error("NULL argument"); return WD_EINVAL; }
+  if (L < 1 || L > WD_LMAX) { wd_set_error("L = %d outside [1, %d]", L, WD_LMAX); return WD_EINVAL; }
+  if (!dev_ptr(R) || !dev_ptr(E)) { wd_set_error("wd_net_loss_grad takes device buffers"); return WD_EINVAL; }
+  const Op& op = *wd_ctx_op(ctx);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long V = op.g.V;
+  NCHECK(net_workspace(n, V, L));
+  // forward, keeping the activations
+  NCU(net_launch_to_cm(static_cast<const double*>(R), n->act[0], (int)V, L, s));
+  NCHECK(net_forward(op, n, L, s));
+  // column weights 1 / (L ||e_i||^2), loss and delta = d loss / d conj(y)
+  double2* npart = reinterpret_cast<double2*>(n->norms);
+  double* norm2 = n->norms + 2 * (size_t)PART_STRIDE * NET_BLOCKS;
+  NCU(launch_colnorms(static_cast<const double*>(E), L, V * 12, npart, norm2, s));
+  wcol_kernel<<<1, 32, 0, s>>>(norm2, n->wcol, L);
+  NCU(cudaGetLastError());
+  NCU(net_launch_loss_delta(n->act[n->layers], static_cast<const double*>(E), n->wcol, n->dA,
+                            n->lpart, NET_BLOCKS, n->loss, (int)V, L, s));
+  // backward through the layers
+  float* delta = n->dA;
+  float* other = n->dB;
+  for (int l = n->layers - 1; l >= 0; --l) {
+    const int cin = n->ch[l], cout = n->ch[l + 1];
+    NCU(net_launch_wgrad(op, n->act[l], delta, cin, cout, L, n->wpart, NET_BLOCKS, n->G + n->off[l], s));
+    if (l > 0) {
+      NCU(net_launch_adjoint_weights(n->W + n->off[l], n->Wadj + n->off[l], cin, cout, s));
+      NCU(net_launch_layer(op, delta, other, n->Wadj + n->off[l], cout, cin, L, s));
+      float* t = delta;
+      delta = other;
+      other = t;
+    }
+  }
+  if (loss) {
+    NCU(cudaMemcpyAsync(loss, n->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  if (grad) {
+    NCU(cudaMemcpyAsync(grad, n->G, n->nw * sizeof(double2), cudaMemcpyDefault, s));
+  }
+  NCU(cudaStreamSynchronize(s));
+  return WD_OK;
+}
+
+int wd_net_adam_step(wd_net* n, double lr, void* stream) {
+  if (!n || !(lr > 0.0)) { wd_set_error("net is NULL or lr <= 0"); return WD_EINVAL; }
+  n->t += 1;
+  NCU(net_launch_adam(n->W, n->G, n->m, n->v, (int)n->nw, (float)lr, 0.9f, 0.999f, 1e-8f, n->t,
+                      static_cast<cudaStream_t>(stream)));
+  return WD_OK;
+}
+
+}  // extern "C"

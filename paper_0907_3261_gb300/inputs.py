@@ -135,3 +135,33 @@ def gaussian_block(dims, L: int, seed: int = 2) -> np.ndarray:
     v = volume(dims)
     return np.ascontiguousarray(
         complex_gaussian(seed, STREAM_VECTOR, v * 12 * L).reshape(v, 4, 3, L))
+
+
+STREAM_WEIGHTS = 0x57474854        # "WGHT"
+
+
+def network_channels(layers: int = 4, hidden: int = 4):
+    """Channel counts (1, hidden, ..., hidden, 1) of a network with ``layers`` layers."""
+    return [1] + [hidden] * (layers - 1) + [1]
+
+
+def network_weights(layers: int = 4, hidden: int = 4, seed: int = 0, noise: float = 0.01):
+    """Initial weights of the preconditioner network, one complex array [9][C_out][C_in][4][4] per
+    layer: the on-site (d = 0) blocks start as the identity map of the network (first layer copies
+    the input to every channel, hidden layers are channel-diagonal, the last averages the
+    channels), plus complex Gaussian noise of standard deviation ``noise`` on every entry."""
+    ch = network_channels(layers, hidden)
+    total = sum(9 * ch[i + 1] * ch[i] * 16 for i in range(layers))
+    g = complex_gaussian(seed, STREAM_WEIGHTS, total) * noise
+    out, off = [], 0
+    for i in range(layers):
+        cin, cout = ch[i], ch[i + 1]
+        n = 9 * cout * cin * 16
+        W = g[off:off + n].reshape(9, cout, cin, 4, 4).copy()
+        off += n
+        for co in range(cout):
+            for c in range(cin):
+                if cin == 1 or cout == 1 or co == c:
+                    W[0, co, c] += np.eye(4) * (1.0 / cin if cout == 1 else 1.0)
+        out.append(W)
+    return out
