@@ -142,6 +142,31 @@ int jacobi_precond_noalloc(wd_ctx* ctx, const void* R, void* G, int L, int j, vo
 int bbicggr_solve(wd_ctx* ctx, const void* B, void* X, int L, int j, double tol,
                   const bbicggr_opts* opts, bbicggr_info* info, void* stream);
 
+/* One solve of a batch (bbicggr_solve_batch).  B and X are device buffers; every job has its own
+ * context (jobs may differ in lattice, kappa, c_SW, L, j and precision). */
+typedef struct {
+  wd_ctx* ctx;
+  const void* B;          /* N x L, device */
+  void* X;                /* X_0 in, solution out, device */
+  int L;
+  int j;
+  double tol;
+  bbicggr_opts opts;      /* maxit, div_thresh, precision, stall_window, net, history are used;
+                             max_restarts is not (see below) */
+  bbicggr_info info;      /* filled on return; rec_resid / true_resid may point to host arrays */
+} bbicggr_job;
+
+/* Preconditioned block BiCGGR for several independent systems at once, with the iteration
+ * controlled on the device: all jobs are branches of one CUDA graph in which each solve's outer
+ * iteration is a conditional while-node (the convergence test of the algorithm box runs in a
+ * kernel that sets the loop condition), so the host launches once and synchronises once.
+ * Differences from bbicggr_solve: no true-residual restarts and no precision fallback -- a job
+ * whose recursive residual converged but whose true residual is above tol, or whose FP32 / network
+ * preconditioner stalled, reports WD_NOT_CONVERGED (solve it again with bbicggr_solve from X).
+ * info.mvm_actual is -1.  Returns WD_OK if every job converged, else the first job's non-OK
+ * status; argument and CUDA errors return before any work. */
+int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream);
+
 void bbicggr_default_opts(bbicggr_opts* opts);
 const char* wd_strerror(int code);
 const char* wd_last_error(void);

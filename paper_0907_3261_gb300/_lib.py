@@ -43,6 +43,11 @@ class Info(C.Structure):
                 ("history_count", C.c_int), ("seconds", C.c_double), ("fallbacks", C.c_int)]
 
 
+class Job(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("B", C.c_void_p), ("X", C.c_void_p), ("L", C.c_int),
+                ("j", C.c_int), ("tol", C.c_double), ("opts", Opts), ("info", Info)]
+
+
 _lib = None
 
 
@@ -70,6 +75,8 @@ def lib():
     L.jacobi_precond.argtypes = [vp, vp, vp, i, i, i, vp]
     L.bbicggr_solve.argtypes = [vp, vp, vp, i, i, d, C.POINTER(Opts), C.POINTER(Info), vp]
     L.jacobi_precond_noalloc.argtypes = [vp, vp, vp, i, i, vp]
+    L.bbicggr_solve_batch.argtypes = [C.POINTER(Job), C.c_int, vp]
+    L.bbicggr_solve_batch.restype = C.c_int
     L.bbicggr_default_opts.argtypes = [C.POINTER(Opts)]
     L.bbicggr_default_opts.restype = None
     L.wd_strerror.argtypes = [i]
@@ -397,3 +404,55 @@ def wd_net_loss_grad(ctx: Context, net: Net, R, E, want_grad: bool = True, strea
 
 def wd_net_adam_step(net: Net, lr: float, stream=None) -> None:
     _check(lib().wd_net_adam_step(net.handle, float(lr), _stream(stream)))
+
+
+
+def bbicggr_solve_batch(jobs, stream=None):
+    """Solve several independent systems in one CUDA graph with device-side iteration control.
+
+    ``jobs``: list of dicts with keys ctx, B, X (device torch tensors; X holds X_0), and optional
+    j (12), tol (1e-12), maxit, div_thresh, precision, stall_window, net, history.  Returns the list
+    of info dicts (same keys as bbicggr_solve's, without restarts/fallbacks semantics)."""
+    n = len(jobs)
+    arr = (Job * n)()
+    keep = []
+    for i, jb in enumerate(jobs):
+        pb, L, kb = _ptr_and_L(jb["B"], "B")
+        px, _, kx = _ptr_and_L(jb["X"], "X")
+        o = Opts()
+        lib().bbicggr_default_opts(C.byref(o))
+        o.maxit = int(jb.get("maxit", 10000))
+        o.div_thresh = float(jb.get("div_thresh", 1e2))
+        o.precision = int(jb.get("precision", 0))
+        o.stall_window = int(jb.get("stall_window", 16))
+        if jb.get("net") is not None:
+            o.net = jb["net"].handle
+        hist = (C.c_double * max(int(jb.get("history", 0)), 1))()
+        if jb.get("history", 0):
+            o.history = C.cast(hist, C.POINTER(C.c_double))
+            o.history_len = int(jb["history"])
+        rec = (C.c_double * L)()
+        tru = (C.c_double * L)()
+        arr[i].ctx = jb["ctx"].handle
+        arr[i].B = pb
+        arr[i].X = px
+        arr[i].L = L
+        arr[i].j = int(jb.get("j", 12))
+        arr[i].tol = float(jb.get("tol", 1e-12))
+        arr[i].opts = o
+        arr[i].info.rec_resid = C.cast(rec, C.POINTER(C.c_double))
+        arr[i].info.true_resid = C.cast(tru, C.POINTER(C.c_double))
+        keep.append((kb, kx, hist, rec, tru))
+    rc = lib().bbicggr_solve_batch(arr, n, _stream(stream))
+    if rc not in SOLVER_STATUSES:
+        _raise(rc)
+    out = []
+    for i in range(n):
+        info = arr[i].info
+        hist, rec, tru = keep[i][2], keep[i][3], keep[i][4]
+        out.append(dict(status=info.status, status_name=lib().wd_strerror(info.status).decode(),
+                        iters=info.iters, mvm_paper=info.mvm_paper,
+                        max_rec_resid=info.max_rec_resid, max_true_resid=info.max_true_resid,
+                        rec_resid=np.array(rec[:]), true_resid=np.array(tru[:]),
+                        history=np.array(hist[:info.history_count]), seconds=info.seconds))
+    return out

@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -120,6 +121,11 @@ struct wd_ctx {
   int tile_r[WD_LMAX + 1] = {};
   int tile_block[WD_LMAX + 1] = {};
   wd_net* active_net = nullptr;   // learned preconditioner of the running solve (mode 2)
+  // device-controlled (graph) solves
+  void* gctl = nullptr;           // GraphCtl
+  double* ghist = nullptr;        // residual history, ghist_len entries
+  int ghist_len = 0;
+  cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
@@ -485,6 +491,9 @@ void wd_destroy(wd_ctx* c) {
   c->stage_out.release();
   cudaFree(c->st);
   cudaFree(c->bnorm2_dev);
+  cudaFree(c->gctl);
+  cudaFree(c->ghist);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   cudaFreeHost(c->hm);
   delete c;
 }
@@ -771,3 +780,319 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
 }
 
 }  // extern "C"
+
+// ================================================================== device-controlled solves
+// bbicggr_solve_batch: every job's solve becomes one branch of a single CUDA graph.  The outer
+// iteration is a conditional WHILE node whose body runs the iteration up to the R update and a
+// check kernel; the check kernel counts k, records the residual, decides (converged, diverged,
+// stalled, maxit, breakdown) and sets both the loop condition and the condition of an IF node that
+// holds the rest of the iteration (F = MR, W = AF, gamma, P, V).  The host launches the graph once
+// and synchronises once for all jobs.
+namespace {
+
+struct GraphCtl {
+  int k, maxit, stall, k_best, status, L, hist_len, pad;
+  double tol, div, best;
+  double bnorm2[WD_LMAX];
+  double rec[WD_LMAX];
+  double true2[WD_LMAX];
+};
+
+__device__ double graph_max_rel(const double* n2, GraphCtl* g) {
+  double m = 0.0;
+  for (int i = 0; i < g->L; ++i) {
+    const double r = sqrt(n2[i]) / sqrt(g->bnorm2[i]);
+    g->rec[i] = r;
+    if (!(r <= m)) m = r;
+  }
+  return m;
+}
+
+__global__ void graph_init_check(const SolverState* st, GraphCtl* g, double* hist,
+                                 cudaGraphConditionalHandle hloop) {
+  if (threadIdx.x != 0) return;
+  const double m = graph_max_rel(st->rnorm2, g);
+  g->k = 0;
+  g->best = m;
+  g->k_best = 0;
+  if (hist && g->hist_len > 0) hist[0] = m;
+  int done = 0, status = WD_OK;
+  if (!isfinite(m)) { done = 1; status = WD_BREAKDOWN; }
+  else if (m <= g->tol) { done = 1; status = WD_OK; }
+  else if (g->maxit <= 0) { done = 1; status = WD_NOT_CONVERGED; }
+  g->status = status;
+  cudaGraphSetConditional(hloop, done ? 0u : 1u);
+}
+
+__global__ void graph_iter_check(const SolverState* st, GraphCtl* g, double* hist,
+                                 cudaGraphConditionalHandle hloop, cudaGraphConditionalHandle htail) {
+  if (threadIdx.x != 0) return;
+  int done = 0, status = WD_OK;
+  if (st->status != ST_OK) {
+    done = 1;
+    status = WD_BREAKDOWN;                    // the update was skipped: k stays
+  } else {
+    g->k += 1;
+    const double m = graph_max_rel(st->rnorm2, g);
+    if (hist && g->k < g->hist_len) hist[g->k] = m;
+    if (!isfinite(m)) { done = 1; status = WD_BREAKDOWN; }
+    else if (m <= g->tol) { done = 1; status = WD_OK; }
+    else if (m > g->div) { done = 1; status = WD_DIVERGED; }
+    else {
+      if (m < g->best) { g->best = m; g->k_best = g->k; }
+      if ((g->stall > 0 && g->k - g->k_best >= g->stall) || g->k >= g->maxit) {
+        done = 1;
+        status = WD_NOT_CONVERGED;
+      }
+    }
+  }
+  g->status = status;
+  cudaGraphSetConditional(hloop, done ? 0u : 1u);
+  cudaGraphSetConditional(htail, done ? 0u : 1u);
+}
+
+// Enqueue `fn` on the context's capture stream as nodes of graph `g` after `deps`; the leaf nodes
+// of what was captured are returned in *leaves.
+template <class Fn>
+int capture_into(wd_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, Fn fn,
+                 std::vector<cudaGraphNode_t>* leaves) {
+  cudaStream_t s = c->capture_stream;
+  CU(cudaStreamBeginCaptureToGraph(s, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                   deps.size(), cudaStreamCaptureModeThreadLocal));
+  int rc = fn(s);
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* d = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &d, nullptr, &nd);
+  if (e == cudaSuccess && leaves) leaves->assign(d, d + nd);
+  cudaGraph_t out = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(s, &out);
+  if (rc != WD_OK) return rc;
+  CU(e);
+  CU(e2);
+  return WD_OK;
+}
+
+// M applied so that the result always lands in `out` (fixed buffers for a graph body).
+int precondition_into(wd_ctx* c, const double* R, double* out, double* tmp, int L, int j,
+                      int precision, cudaStream_t s) {
+  const bool to_tmp_first = precision == 0 && j > 0 && j % 2 == 0;
+  double* res = nullptr;
+  CHECK(precondition(c, R, to_tmp_first ? tmp : out, to_tmp_first ? out : tmp, &res, L, j,
+                     precision, nullptr, s));
+  if (res != out) { set_err("internal: preconditioner result buffer"); return WD_ECUDA; }
+  return WD_OK;
+}
+
+struct JobPtrs {
+  const double* B;
+  double* X;
+  int L, j, mode;
+  double tol;
+};
+
+int build_job(wd_ctx* c, const JobPtrs& jp, cudaGraph_t G) {
+  const Op& op = c->op;
+  const int L = jp.L, j = jp.j, mode = jp.mode;
+  const long long rows = (long long)op.g.V * 12;
+  const size_t bytes = block_bytes(c, L);
+  double* R = c->blk[B_R].d();
+  double* P = c->blk[B_P].d();
+  double* V = c->blk[B_V].d();
+  double* W = c->blk[B_W].d();
+  double* U = c->blk[B_U].d();
+  double* Y = c->blk[B_Y].d();
+  double* Rt = c->blk[B_RT].d();
+  double* F = c->blk[B_F].d();
+  double* Gk = c->blk[B_G].d();
+  double* T = c->blk[B_T].d();
+  double2* part = static_cast<double2*>(c->part.p);
+  SolverState* st = c->st;
+  GraphCtl* g = static_cast<GraphCtl*>(c->gctl);
+  double* hist = c->ghist;
+
+  cudaGraphConditionalHandle hloop;
+  CU(cudaGraphConditionalHandleCreate(&hloop, G, 1, cudaGraphCondAssignDefault));
+  std::vector<cudaGraphNode_t> pre_leaves, a_leaves, dummy;
+  // before the loop: R_0, P_0, R~_0, R~_0^H R_0, the first check, F_0, V_0 = W_0, traces, R~_0^H V_0
+  CHECK(capture_into(c, G, {}, [&](cudaStream_t s) -> int {
+    CU(cudaMemsetAsync(&st->status, 0, sizeof(int), s));
+    LAUNCH(WD_K_COLNORM, 2, launch_colnorms(jp.B, L, rows, part, g->bnorm2, s));
+    LAUNCH(WD_K_RESID, 1, launch_resid_f64(op, jp.X, jp.B, R, L, s));
+    LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(P, R, bytes, cudaMemcpyDeviceToDevice, s));
+    LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(Rt, R, bytes, cudaMemcpyDeviceToDevice, s));
+    LAUNCH(WD_K_GRAM, 2, launch_gram(Rt, R, L, rows, part, st, GRAM_RTR, true, s));
+    graph_init_check<<<1, 32, 0, s>>>(st, g, hist, hloop);
+    CU(cudaGetLastError());
+    CHECK(precondition_into(c, R, F, T, L, j, mode, s));
+    LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, F, W, L, s));
+    LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(V, W, bytes, cudaMemcpyDeviceToDevice, s));
+    LAUNCH(WD_K_TRACE, 2, launch_traces(W, R, L, rows, part, st, s));
+    LAUNCH(WD_K_GRAM, 2, launch_gram(Rt, V, L, rows, part, st, GRAM_RTV, false, s));
+    return WD_OK;
+  }, &pre_leaves));
+  // the outer iteration
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hloop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t nwhile;
+  CU(cudaGraphAddNode(&nwhile, G, pre_leaves.data(), nullptr, pre_leaves.size(), &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  cudaGraphConditionalHandle htail;
+  CU(cudaGraphConditionalHandleCreate(&htail, body, 0, 0));
+  CHECK(capture_into(c, body, {}, [&](cudaStream_t s) -> int {
+    LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_alpha(st, L, s));
+    LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(P, V, U, L, rows, st, s));
+    CHECK(precondition_into(c, U, Gk, T, L, j, mode, s));
+    LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, Gk, Y, L, s));
+    LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(jp.X, F, Gk, R, W, Y, Rt, L, rows, part, st, s));
+    graph_iter_check<<<1, 32, 0, s>>>(st, g, hist, hloop, htail);
+    CU(cudaGetLastError());
+    return WD_OK;
+  }, &a_leaves));
+  cudaGraphNodeParams ip = {};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = htail;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  cudaGraphNode_t nif;
+  CU(cudaGraphAddNode(&nif, body, a_leaves.data(), nullptr, a_leaves.size(), &ip));
+  cudaGraph_t tail = ip.conditional.phGraph_out[0];
+  CHECK(capture_into(c, tail, {}, [&](cudaStream_t s) -> int {
+    CHECK(precondition_into(c, R, F, T, L, j, mode, s));
+    LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, F, W, L, s));
+    LAUNCH(WD_K_TRACE, 2, launch_traces(W, R, L, rows, part, st, s));
+    LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_gamma(st, L, s));
+    LAUNCH(WD_K_UPDATE_PV, 2, launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s));
+    return WD_OK;
+  }, &dummy));
+  // after the loop: the true residual
+  CHECK(capture_into(c, G, {nwhile}, [&](cudaStream_t s) -> int {
+    LAUNCH(WD_K_RESID, 1, launch_resid_f64(op, jp.X, jp.B, T, L, s));
+    LAUNCH(WD_K_COLNORM, 2, launch_colnorms(T, L, rows, part, g->true2, s));
+    return WD_OK;
+  }, &dummy));
+  return WD_OK;
+}
+
+}  // namespace
+
+extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!jobs || njobs < 1) { set_err("no jobs"); return WD_EINVAL; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < njobs; ++i) {
+    bbicggr_job& jb = jobs[i];
+    wd_ctx* c = jb.ctx;
+    if (!c) { set_err("job %d: ctx is NULL", i); return WD_EINVAL; }
+    for (int k = 0; k < i; ++k)
+      if (jobs[k].ctx == c) { set_err("jobs %d and %d share a context", k, i); return WD_EINVAL; }
+    CHECK(check_L(jb.L));
+    if (jb.j < 0 || !(jb.tol > 0.0)) { set_err("job %d: j < 0 or tol <= 0", i); return WD_EINVAL; }
+    if (!jb.B || !jb.X || !is_device_ptr(jb.B) || !is_device_ptr(jb.X)) {
+      set_err("job %d: B and X must be device buffers", i);
+      return WD_EINVAL;
+    }
+    const bbicggr_opts& o = jb.opts;
+    if (o.maxit < 0 || !(o.div_thresh > 0.0) || o.stall_window < 0 ||
+        (o.precision != 0 && o.precision != 1)) {
+      set_err("job %d: invalid options", i);
+      return WD_EINVAL;
+    }
+  }
+  // workspace, tuning, network buffers and control blocks before any capture
+  for (int i = 0; i < njobs; ++i) {
+    bbicggr_job& jb = jobs[i];
+    wd_ctx* c = jb.ctx;
+    CHECK(ensure_workspace(c, jb.L));
+    const int mode = jb.opts.net ? 2 : jb.opts.precision;
+    if (mode == 1 && jb.j >= 2) CHECK(ensure_workspace32(c, jb.L, s));
+    if (mode == 2) CHECK(wd_net_prepare(c, jb.opts.net, jb.L));
+    if (!c->gctl) CU(cudaMalloc(&c->gctl, sizeof(GraphCtl)));
+    const int hl = jb.opts.history ? jb.opts.history_len : 0;
+    if (hl > c->ghist_len) {
+      cudaFree(c->ghist);
+      c->ghist = nullptr;
+      c->ghist_len = 0;
+      CU(cudaMalloc(&c->ghist, hl * sizeof(double)));
+      c->ghist_len = hl;
+    }
+    if (!c->capture_stream) CU(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    GraphCtl h = {};
+    h.maxit = jb.opts.maxit;
+    h.stall = mode != 0 ? jb.opts.stall_window : 0;
+    h.L = jb.L;
+    h.hist_len = hl;
+    h.tol = jb.tol;
+    h.div = jb.opts.div_thresh;
+    CU(cudaMemcpyAsync(c->gctl, &h, sizeof(GraphCtl), cudaMemcpyHostToDevice, s));
+  }
+  CU(cudaStreamSynchronize(s));
+  cudaGraph_t G = nullptr;
+  CU(cudaGraphCreate(&G, 0));
+  int rc = WD_OK;
+  for (int i = 0; i < njobs && rc == WD_OK; ++i) {
+    bbicggr_job& jb = jobs[i];
+    wd_ctx* c = jb.ctx;
+    const bool timing = c->prof.timing;
+    c->prof.timing = false;                 // no event nodes in the graph
+    c->active_net = jb.opts.net;
+    JobPtrs jp{static_cast<const double*>(jb.B), static_cast<double*>(jb.X), jb.L, jb.j,
+               jb.opts.net ? 2 : jb.opts.precision, jb.tol};
+    rc = build_job(c, jp, G);
+    c->prof.timing = timing;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (rc == WD_OK) {
+    cudaError_t e = cudaGraphInstantiate(&exec, G, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_err("graph solve failed: %s", cudaGetErrorString(e));
+      rc = WD_ECUDA;
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(G);
+  if (rc != WD_OK) return rc;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int worst = WD_OK;
+  for (int i = 0; i < njobs; ++i) {
+    bbicggr_job& jb = jobs[i];
+    wd_ctx* c = jb.ctx;
+    GraphCtl h;
+    CU(cudaMemcpy(&h, c->gctl, sizeof(GraphCtl), cudaMemcpyDeviceToHost));
+    bbicggr_info& in = jb.info;
+    const int jeff = jb.opts.net ? 0 : jb.j;
+    double mtrue = 0.0, mrec = 0.0;
+    double tr[WD_LMAX];
+    for (int k = 0; k < jb.L; ++k) {
+      tr[k] = std::sqrt(h.true2[k]) / std::sqrt(h.bnorm2[k]);
+      if (!(tr[k] <= mtrue)) mtrue = tr[k];
+      if (!(h.rec[k] <= mrec)) mrec = h.rec[k];
+    }
+    int status = h.status;
+    if (status == WD_OK && !(mtrue <= jb.tol)) status = WD_NOT_CONVERGED;
+    in.status = status;
+    in.iters = h.k;
+    in.restarts = 0;
+    in.fallbacks = 0;
+    in.mvm_paper = (long long)jb.L * (2LL * (jeff + 1) * h.k + 1);
+    in.mvm_actual = -1;
+    in.max_rec_resid = mrec;
+    in.max_true_resid = mtrue;
+    if (in.rec_resid) std::memcpy(in.rec_resid, h.rec, jb.L * sizeof(double));
+    if (in.true_resid) std::memcpy(in.true_resid, tr, jb.L * sizeof(double));
+    in.history_count = 0;
+    if (jb.opts.history && h.hist_len > 0) {
+      const int n = std::min(h.k + 1, h.hist_len);
+      CU(cudaMemcpy(jb.opts.history, c->ghist, n * sizeof(double), cudaMemcpyDeviceToHost));
+      in.history_count = n;
+    }
+    in.seconds = secs;
+    if (status != WD_OK && worst == WD_OK) worst = status;
+  }
+  return worst;
+}

@@ -108,3 +108,4 @@ cudaError_t net_launch_adam(float2* W, const double2* G, float2* m, float2* v, i
 struct wd_net;
 int wd_net_precondition(wd_ctx* ctx, wd_net* net, const double* R, double* G, int L,
                         cudaStream_t s);
+int wd_net_prepare(wd_ctx* ctx, wd_net* net, int L);

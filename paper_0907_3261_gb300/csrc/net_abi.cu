@@ -140,6 +140,11 @@ int set_weights(wd_net* n, const void* w) {
 
 }  // namespace
 
+// Internal: allocate the network's workspace for this lattice and L (before a stream capture).
+int wd_net_prepare(wd_ctx* ctx, wd_net* n, int L) {
+  return net_workspace(n, wd_ctx_op(ctx)->g.V, L);
+}
+
 // Internal: G = N(R) for device blocks R, G (site-major FP64), used by the solver.
 int wd_net_precondition(wd_ctx* ctx, wd_net* n, const double* R, double* G, int L, cudaStream_t s) {
   const Op& op = *wd_ctx_op(ctx);
