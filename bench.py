@@ -227,6 +227,82 @@ def config(args):
             "l2": "working set 13 blocks x 302 MB > L2 (no flush needed)"}
 
 
+# ---------------------------------------------------------------- 24 solves in one graph
+BATCH_LATTICES = [(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32), (32, 32, 32, 64)]
+BATCH_L = [1, 3, 7, 12]
+
+
+def batch_jobs():
+    """24 solves: every lattice with every L, and the two smaller lattices once more; kappa spread
+    evenly over [0.115, 0.124]."""
+    combos = [(d, L) for d in BATCH_LATTICES for L in BATCH_L]
+    combos += [(d, L) for d in BATCH_LATTICES[:2] for L in BATCH_L]
+    return [(d, L, 0.115 + 0.009 * i / (len(combos) - 1)) for i, (d, L) in enumerate(combos)]
+
+
+def batch_workload(args):
+    """Time for 24 independent solves launched as one CUDA graph (device-side iteration control),
+    against the same 24 solves run one after another with host-side control."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0907_3261_gb300 as wd
+    from paper_0907_3261_gb300 import inputs as I
+    dev = torch.device("cuda", 0)
+    j = 8
+    links = {d: torch.from_numpy(I.random_links(d, LINK_EPS, seed=0)).to(dev) for d in BATCH_LATTICES}
+    jobs = []
+    for n, (d, L, kappa) in enumerate(batch_jobs()):
+        ctx = wd.wd_create(links[d], d, kappa, CSW)
+        B = torch.from_numpy(I.z4_noise(d, L, seed=100 + n)).to(dev)
+        jobs.append(dict(ctx=ctx, B=B, X=torch.zeros_like(B), j=j, precision=1, tol=TOL))
+    del links
+    site_rhs = sum(int(np.prod(d)) * L for d, L, _ in batch_jobs())
+
+    def run_graph():
+        for jb in jobs:
+            jb["X"].zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = wd.bbicggr_solve_batch(jobs)
+        return time.perf_counter() - t0, infos
+
+    def run_sequential():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = []
+        for jb in jobs:
+            jb["X"].zero_()
+            infos.append(wd.bbicggr_solve(jb["ctx"], jb["B"], jb["X"], j=j, tol=TOL, precision=1)[1])
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, infos
+
+    for _ in range(args.warmup):
+        run_graph()
+    tg = [run_graph() for _ in range(args.steps)]
+    ts = [run_sequential() for _ in range(max(1, args.steps // 2))]
+    g_s = statistics.mean(t for t, _ in tg)
+    s_s = statistics.mean(t for t, _ in ts)
+    infos = tg[-1][1]
+    ok = all(i["status"] == wd.WD_OK for i in infos)
+    out = {"metric": "time for 24 independent solves (one CUDA graph)", "value": round(g_s, 4),
+           "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(g_s * 1e3, 2), "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+           "config": {"workload": "batch24: lattices 8^4, 12^3x24, 16^3x32, 32^3x64 x L in {1,3,7,12} "
+                                  "(+ 8^4 and 12^3x24 again), kappa 0.115..0.124, Jacobi j=8 in FP32, "
+                                  "true resid <= 1e-12",
+                      "jobs": len(jobs), "site_rhs_total": site_rhs},
+           "sequential_host_controlled_s": round(s_s, 4),
+           "speedup_vs_sequential": round(s_s / g_s, 3),
+           "solves": {"status": "ok" if ok else "FAILED",
+                      "iters": [i["iters"] for i in infos],
+                      "max_true_resid": max(i["max_true_resid"] for i in infos)}}
+    print(json.dumps(out), flush=True)
+    return 0 if ok else 1
+
+
 # ---------------------------------------------------------------- GB300 arm
 def main():
     ap = argparse.ArgumentParser()
@@ -236,11 +312,15 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="tts", choices=["tts", "batch24"],
+                    help="tts: the time-to-solution line; batch24: 24 solves in one CUDA graph")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batch24":
+        return batch_workload(args)
 
     import numpy as np
     import torch

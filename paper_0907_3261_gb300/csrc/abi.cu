@@ -108,7 +108,7 @@ struct wd_ctx {
   int device = 0;
   // solver workspace for the current L
   int L = 0;
-  DevBuf blk[14];          // X R P V W F U G Y Rt T B Xs X0
+  DevBuf blk[13];          // R P V W F U G Y Rt T (always); B Xs X0 (on demand)
   DevBuf part;             // reduction partials
   SolverState* st = nullptr;
   HostMirror* hm = nullptr;
@@ -130,7 +130,8 @@ struct wd_ctx {
 
 namespace {
 
-enum { B_X, B_R, B_P, B_V, B_W, B_F, B_U, B_G, B_Y, B_RT, B_T, B_B, B_XS, B_X0, B_COUNT };
+enum { B_R, B_P, B_V, B_W, B_F, B_U, B_G, B_Y, B_RT, B_T, B_CORE,
+       B_B = B_CORE, B_XS, B_X0, B_COUNT };
 
 size_t block_bytes(const wd_ctx* c, int L) { return (size_t)c->op.g.V * 12 * L * 16; }
 
@@ -206,7 +207,7 @@ int ensure_workspace(wd_ctx* c, int L) {
   for (auto& b : c->blk) b.release();
   c->L = 0;
   const size_t bytes = block_bytes(c, L);
-  for (int i = 0; i < B_COUNT; ++i) CHECK(c->blk[i].ensure(bytes));
+  for (int i = 0; i < B_CORE; ++i) CHECK(c->blk[i].ensure(bytes));
   CHECK(c->part.ensure((size_t)152 * 4 * PART_STRIDE * sizeof(double2)));
   if (!c->st) CU(cudaMalloc(&c->st, sizeof(SolverState)));
   if (!c->bnorm2_dev) CU(cudaMalloc(&c->bnorm2_dev, 2 * WD_LMAX * sizeof(double)));
@@ -689,12 +690,14 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
 
   const double* Bd = static_cast<const double*>(B);
   if (!is_device_ptr(B)) {
+    CHECK(c->blk[B_B].ensure(bytes));
     CU(cudaMemcpyAsync(c->blk[B_B].d(), B, bytes, cudaMemcpyHostToDevice, s));
     Bd = c->blk[B_B].d();
   }
   const bool x_dev = is_device_ptr(X);
   double* Xd = static_cast<double*>(X);
   if (!x_dev) {
+    CHECK(c->blk[B_XS].ensure(bytes));
     Xd = c->blk[B_XS].d();
     CU(cudaMemcpyAsync(Xd, X, bytes, cudaMemcpyHostToDevice, s));
   }
@@ -712,6 +715,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
   int prec = o.net ? 2 : o.precision;
   c->active_net = o.net;
   const bool may_fall_back = prec != 0 && o.stall_window > 0;
+  if (may_fall_back) CHECK(c->blk[B_X0].ensure(bytes));
   if (may_fall_back)   // keep X_0 for a restart with the FP64 preconditioner
     LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(c->blk[B_X0].d(), Xd, bytes, cudaMemcpyDeviceToDevice, s));
   long long mvm_paper = 0, hops = 0;
