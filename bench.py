@@ -5,7 +5,9 @@ Workload (the paper's lattice, Sec. 3.1, with synthetic links in place of its co
 16^3 x 32 periodic lattice, links SU3proj(1 + 0.2 G) (seed 0), c_SW = 1.0, kappa = 0.134, L = 12
 Z4-noise sources (seed 1 + rank), Jacobi j = 12 (the paper's recommended L = 12, j >= 12, Sec. 3.3),
 X_0 = 0, R~_0 = R_0, tolerance 1e-12 on the recursive residual and then on the true residual.
-One step = one complete solve through the C-ABI.  kappa = 0.134 is the largest value of the
+One step = one complete solve through the C-ABI, by default the plain FP64 method (--precision
+mixed: FP32 Jacobi preconditioner with the FP64 outer method); the run also times the other form
+on the same workload for comparison.  kappa = 0.134 is the largest value of the
 0.001-step sweep from 0.115 at which the L = 1, j = 0 solve still converges (660 iterations);
 at 0.135 it no longer does.
 
@@ -310,7 +312,11 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="fp64: the plain FP64 method (the default); mixed: FP32 Jacobi "
+                         "preconditioner with the FP64 outer method")
+    ap.add_argument("--no-other-form", action="store_true",
+                    help="skip timing the other precision form on the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="tts", choices=["tts", "batch24"],
                     help="tts: the time-to-solution line; batch24: 24 solves in one CUDA graph")
@@ -393,6 +399,32 @@ def main():
     e2e_s = maxr((time.perf_counter() - t0) / args.steps)
     block = B.numel() * 16
 
+    # ---- the other precision form on the same workload, for comparison (not the value)
+    other = None
+    if not args.no_other_form:
+        oprec = 1 if prec == 0 else 0
+
+        def solve_other():
+            X.zero_()
+            return wd.bbicggr_solve(ctx, B, X, j=J_JACOBI, tol=TOL, precision=oprec,
+                                    stream=stream)[1]
+        solve_other()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        io = [solve_other() for _ in range(2)]
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        to = maxr(f0.elapsed_time(f1) / 2 / 1e3)
+        ok = ok and all(i["status"] == wd.WD_OK for i in io)
+        other = {"form": "mixed: FP32 Jacobi preconditioner" if oprec else "plain FP64 Jacobi",
+                 "value": round(to, 6), "unit": "s", "iters": io[-1]["iters"],
+                 "fallbacks": io[-1]["fallbacks"],
+                 "max_true_resid": max(i["max_true_resid"] for i in io),
+                 "ratio_to_value": round(to / (ms_step / 1e3), 3)}
+
     # ---- roofline of the dominant kernel class, and of every stencil class
     V = int(np.prod(DIMS))
     peaks = {}
@@ -450,9 +482,12 @@ def main():
                      "restarts": infos[-1]["restarts"],
                      "fallbacks": infos[-1]["fallbacks"]},
            "kernels": {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in prof.items() if n or ms}}
+    if other is not None:
+        out["other_form"] = other
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_apply, t_inv, cores = oracle_sample(L_RHS)
-        k = infos[-1]["iters"]
+        # the oracle runs the plain FP64 method: scale by that method's iteration count
+        k = infos[-1]["iters"] if prec == 0 or other is None else other["iters"]
         out["cpu_baseline"] = {
             "value": round(oracle_tts(k, J_JACOBI, t_apply, t_inv), 3), "unit": "s",
             "cores": cores, "kind": "oracle",

@@ -65,7 +65,10 @@ typedef struct {
   int precision;          /* 0: FP64 preconditioner (default); 1: FP32 preconditioner with FP32
                              accumulation -- the outer recurrences, the products W = AF and
                              Y = AG, the Gram matrices, the L x L solves and the true residual stay
-                             FP64 */
+                             FP64; 2: as 1, and the direction recurrences U = (P - zeta V) alpha,
+                             P = R + U gamma, V = W + Y gamma and the Gram products in double-float
+                             (FP32-pair, ~48-bit) arithmetic on the FP32 pipes, with the X and R
+                             updates and column norms still FP64 */
   double* history;        /* optional host array: max_i ||r_i||/||b_i|| after every R update */
   int history_len;        /* capacity of history (entries beyond it are dropped) */
   int stall_window;       /* precision 1 only: when the max relative residual has not reached a new
@@ -226,7 +229,8 @@ const char* wd_profile_name(int kernel_class);
  * CTA).  The autotuner times every candidate tile once, at the first FP32 preconditioner call with
  * a given L, and keeps the fastest in the context.  WD_EINVAL until then. */
 int wd_tuned_tile(const wd_ctx* ctx, int L, int* rhs_per_thread, int* block);
-/* Sets that tile by hand instead (rhs_per_thread 1 or 2 dividing L; block 64, 128 or 256). */
+/* Sets that tile by hand instead: rhs_per_thread 1 or 2 dividing L with block 64, 128 or 256, or
+ * rhs_per_thread 0 with block 128 -- the stencil of every (site, rhs) pair split over two warps. */
 int wd_set_tile(wd_ctx* ctx, int L, int rhs_per_thread, int block);
 
 /* Lattice size and parameters of a context (for bindings): dims[4], V, kappa, c_SW. */

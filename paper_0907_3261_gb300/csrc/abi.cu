@@ -120,6 +120,7 @@ struct wd_ctx {
   // autotuned tile of the FP32 sweep per L: RHS per thread and threads per CTA (0 = not tuned)
   int tile_r[WD_LMAX + 1] = {};
   int tile_block[WD_LMAX + 1] = {};
+  bool tile_set[WD_LMAX + 1] = {};
   wd_net* active_net = nullptr;   // learned preconditioner of the running solve (mode 2)
   // device-controlled (graph) solves
   void* gctl = nullptr;           // GraphCtl
@@ -219,7 +220,7 @@ int ensure_workspace(wd_ctx* c, int L) {
 // Picks the FP32 sweep's tile (RHS per thread, threads per CTA) for this lattice and L by timing
 // every candidate on the context's FP32 blocks (zeroed first); the winner is kept in the context.
 int autotune_f32(wd_ctx* c, int L, cudaStream_t s) {
-  static const int cand[][2] = {{1, 64}, {1, 128}, {1, 256}, {2, 64}, {2, 128}, {2, 256}};
+  static const int cand[][2] = {{1, 64}, {1, 128}, {1, 256}, {2, 64}, {2, 128}, {2, 256}, {0, 128}};
   const size_t bytes = (size_t)c->op.g.V * 12 * L * 8;
   float* u32 = static_cast<float*>(c->blk32[0].p);
   float* a = static_cast<float*>(c->blk32[1].p);
@@ -233,7 +234,7 @@ int autotune_f32(wd_ctx* c, int L, cudaStream_t s) {
   int best_i = 0;
   cudaError_t err = cudaSuccess;
   for (int i = 0; i < (int)(sizeof(cand) / sizeof(cand[0])) && err == cudaSuccess; ++i) {
-    if (L % cand[i][0] != 0) continue;
+    if (cand[i][0] > 0 && L % cand[i][0] != 0) continue;
     err = launch_jacobi_f32_tiled(c->op, a, u32, b, nullptr, L, cand[i][0], cand[i][1], s);
     if (err == cudaSuccess) err = cudaEventRecord(e0, s);
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
@@ -249,13 +250,14 @@ int autotune_f32(wd_ctx* c, int L, cudaStream_t s) {
   CU(err);
   c->tile_r[L] = cand[best_i][0];
   c->tile_block[L] = cand[best_i][1];
+  c->tile_set[L] = true;
   return WD_OK;
 }
 
 int ensure_workspace32(wd_ctx* c, int L, cudaStream_t s) {
   const size_t bytes = (size_t)c->op.g.V * 12 * L * 8;
   for (auto& b : c->blk32) CHECK(b.ensure(bytes));
-  if (!c->tile_r[L]) CHECK(autotune_f32(c, L, s));
+  if (!c->tile_set[L]) CHECK(autotune_f32(c, L, s));
   return WD_OK;
 }
 
@@ -356,8 +358,8 @@ double max_rel(const double* n2, const double* b2, int L, double* rel) {
 }
 
 // One run of preconditioned block BiCGGR from the current X (Sec. 2, algorithm box).
-int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precision, double tol,
-                int maxit, double div_thresh, const double* b2, bbicggr_opts* o, int* hist_n,
+int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precision, bool df,
+                double tol, int maxit, double div_thresh, const double* b2, bbicggr_opts* o, int* hist_n,
                 long long* hop_count, RunResult* out, cudaStream_t s) {
   const Op& op = c->op;
   const long long rows = (long long)op.g.V * 12;
@@ -406,12 +408,12 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
   for (;;) {
     if (k >= maxit) { out->status = WD_NOT_CONVERGED; break; }
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_alpha(st, L, s));                       // alpha_k, zeta_k
-    LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(P, V, U, L, rows, st, s));           // U_k = (P_k - zeta_k V_k) alpha_k
+    LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(P, V, U, L, rows, st, s, df));           // U_k = (P_k - zeta_k V_k) alpha_k
     CHECK(precondition(c, U, pG, pT, &res, L, j, precision, hop_count, s));   // G_k = M U_k
     if (res != pG) { pT = pG; pG = res; }
     LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pG, Y, L, s));                  // Y_k = A G_k
     ++*hop_count;
-    LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(X, pF, pG, R, W, Y, Rt, L, rows, part, st, s));   // X_{k+1}, R_{k+1}
+    LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(X, pF, pG, R, W, Y, Rt, L, rows, part, st, s, df));   // X_{k+1}, R_{k+1}
     CHECK(read_back(c, s));
     if (c->hm->status != ST_OK) { out->status = WD_BREAKDOWN; break; }
     ++k;
@@ -428,7 +430,7 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
     ++*hop_count;
     LAUNCH(WD_K_TRACE, 2, launch_traces(W, R, L, rows, part, st, s));          // Tr[W^H R], Tr[W^H W]
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_gamma(st, L, s));                       // gamma_k
-    LAUNCH(WD_K_UPDATE_PV, 2, launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s));   // P_{k+1}, V_{k+1}
+    LAUNCH(WD_K_UPDATE_PV, 2, launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s, df));   // P_{k+1}, V_{k+1}
   }
   out->k = k;
   return WD_OK;
@@ -486,7 +488,7 @@ void wd_destroy(wd_ctx* c) {
   cudaFree(c->op.clov_inv32);
   for (auto& b : c->blk) b.release();
   for (auto& b : c->blk32) b.release();
-  for (int l = 0; l <= WD_LMAX; ++l) c->tile_r[l] = c->tile_block[l] = 0;
+  for (int l = 0; l <= WD_LMAX; ++l) { c->tile_r[l] = c->tile_block[l] = 0; c->tile_set[l] = false; }
   c->part.release();
   c->stage_in.release();
   c->stage_out.release();
@@ -588,18 +590,20 @@ const char* wd_profile_name(int cls) {
 int wd_set_tile(wd_ctx* c, int L, int rhs_per_thread, int block) {
   if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
   CHECK(check_L(L));
-  if ((rhs_per_thread != 1 && rhs_per_thread != 2) || L % rhs_per_thread != 0 ||
-      (block != 64 && block != 128 && block != 256)) {
+  const bool split = rhs_per_thread == 0 && block == 128;
+  if (!split && ((rhs_per_thread != 1 && rhs_per_thread != 2) || L % rhs_per_thread != 0 ||
+                 (block != 64 && block != 128 && block != 256))) {
     set_err("tile (%d RHS/thread, %d threads) not available for L = %d", rhs_per_thread, block, L);
     return WD_EINVAL;
   }
   c->tile_r[L] = rhs_per_thread;
   c->tile_block[L] = block;
+  c->tile_set[L] = true;
   return WD_OK;
 }
 
 int wd_tuned_tile(const wd_ctx* c, int L, int* rhs_per_thread, int* block) {
-  if (!c || L < 1 || L > WD_LMAX || !c->tile_r[L]) { set_err("no tuned tile for this L"); return WD_EINVAL; }
+  if (!c || L < 1 || L > WD_LMAX || !c->tile_set[L]) { set_err("no tuned tile for this L"); return WD_EINVAL; }
   if (rhs_per_thread) *rhs_per_thread = c->tile_r[L];
   if (block) *block = c->tile_block[L];
   return WD_OK;
@@ -682,7 +686,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     set_err("invalid options");
     return WD_EINVAL;
   }
-  if (o.precision != 0 && o.precision != 1) { set_err("precision %d not in {0, 1}", o.precision); return WD_EINVAL; }
+  if (o.precision < 0 || o.precision > 2) { set_err("precision %d not in {0, 1, 2}", o.precision); return WD_EINVAL; }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CHECK(ensure_workspace(c, L));
   const size_t bytes = block_bytes(c, L);
@@ -712,7 +716,8 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     }
 
   int status = WD_OK, iters = 0, restarts = 0, hist_n = 0, fallbacks = 0;
-  int prec = o.net ? 2 : o.precision;
+  int prec = o.net ? 2 : (o.precision >= 1 ? 1 : 0);
+  bool df = o.precision == 2;
   c->active_net = o.net;
   const bool may_fall_back = prec != 0 && o.stall_window > 0;
   if (may_fall_back) CHECK(c->blk[B_X0].ensure(bytes));
@@ -724,7 +729,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
   double mtrue = 0.0;
   for (;;) {
     long long hop_run = 0;
-    CHECK(run_bbicggr(c, Bd, Xd, L, j, prec, tol, o.maxit - iters, o.div_thresh, b2, &o, &hist_n,
+    CHECK(run_bbicggr(c, Bd, Xd, L, j, prec, df, tol, o.maxit - iters, o.div_thresh, b2, &o, &hist_n,
                       &hop_run, &rr, s));
     iters += rr.k;
     hops += hop_run;
@@ -737,6 +742,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
       // which block BiCGGR (with R~_0 = R_0 or the original R~_0) itself fails to converge.
       LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(Xd, c->blk[B_X0].d(), bytes, cudaMemcpyDeviceToDevice, s));
       prec = 0;
+      df = false;
       ++fallbacks;
       continue;
     }
@@ -892,6 +898,7 @@ struct JobPtrs {
   const double* B;
   double* X;
   int L, j, mode;
+  bool df;
   double tol;
 };
 
@@ -948,10 +955,10 @@ int build_job(wd_ctx* c, const JobPtrs& jp, cudaGraph_t G) {
   CU(cudaGraphConditionalHandleCreate(&htail, body, 0, 0));
   CHECK(capture_into(c, body, {}, [&](cudaStream_t s) -> int {
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_alpha(st, L, s));
-    LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(P, V, U, L, rows, st, s));
+    LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(P, V, U, L, rows, st, s, jp.df));
     CHECK(precondition_into(c, U, Gk, T, L, j, mode, s));
     LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, Gk, Y, L, s));
-    LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(jp.X, F, Gk, R, W, Y, Rt, L, rows, part, st, s));
+    LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(jp.X, F, Gk, R, W, Y, Rt, L, rows, part, st, s, jp.df));
     graph_iter_check<<<1, 32, 0, s>>>(st, g, hist, hloop, htail);
     CU(cudaGetLastError());
     return WD_OK;
@@ -969,7 +976,7 @@ int build_job(wd_ctx* c, const JobPtrs& jp, cudaGraph_t G) {
     LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, F, W, L, s));
     LAUNCH(WD_K_TRACE, 2, launch_traces(W, R, L, rows, part, st, s));
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_gamma(st, L, s));
-    LAUNCH(WD_K_UPDATE_PV, 2, launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s));
+    LAUNCH(WD_K_UPDATE_PV, 2, launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s, jp.df));
     return WD_OK;
   }, &dummy));
   // after the loop: the true residual
@@ -1001,7 +1008,7 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     }
     const bbicggr_opts& o = jb.opts;
     if (o.maxit < 0 || !(o.div_thresh > 0.0) || o.stall_window < 0 ||
-        (o.precision != 0 && o.precision != 1)) {
+        o.precision < 0 || o.precision > 2) {
       set_err("job %d: invalid options", i);
       return WD_EINVAL;
     }
@@ -1011,7 +1018,7 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     bbicggr_job& jb = jobs[i];
     wd_ctx* c = jb.ctx;
     CHECK(ensure_workspace(c, jb.L));
-    const int mode = jb.opts.net ? 2 : jb.opts.precision;
+    const int mode = jb.opts.net ? 2 : (jb.opts.precision >= 1 ? 1 : 0);
     if (mode == 1 && jb.j >= 2) CHECK(ensure_workspace32(c, jb.L, s));
     if (mode == 2) CHECK(wd_net_prepare(c, jb.opts.net, jb.L));
     if (!c->gctl) CU(cudaMalloc(&c->gctl, sizeof(GraphCtl)));
@@ -1044,7 +1051,7 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     c->prof.timing = false;                 // no event nodes in the graph
     c->active_net = jb.opts.net;
     JobPtrs jp{static_cast<const double*>(jb.B), static_cast<double*>(jb.X), jb.L, jb.j,
-               jb.opts.net ? 2 : jb.opts.precision, jb.tol};
+               jb.opts.net ? 2 : (jb.opts.precision >= 1 ? 1 : 0), jb.opts.precision == 2, jb.tol};
     rc = build_job(c, jp, G);
     c->prof.timing = timing;
   }

@@ -376,6 +376,148 @@ update_pv_kernel(double* __restrict__ P, double* __restrict__ V, const double* _
   write_partial(part, L, acc, nacc, false);
 }
 
+// ---------------------------------------------------------------- double-float variants
+// The same three updates with every product of an N x L block by an L x L matrix, and the Gram
+// products, in double-float arithmetic (FP32 pairs, ~48 bits) on the FP32 pipes.  The X and R
+// updates and the column norms stay FP64: X and R are updated with the F, G whose products with A
+// are subtracted from R, so R = B - AX holds to FP64 rounding whatever precision the directions
+// U, P, V and the coefficients alpha, gamma are computed in.
+WD_DEV CDF ldcdf(const double* p, size_t e) { return cdf_from(ld2(p, e)); }
+WD_DEV CDF cdf_of(double2 v) { return cdf_from(Cx<double>{v.x, v.y}); }
+WD_DEV double2 d2_of(CDF z) {
+  const Cx<double> c = cdf_to({df_norm(z.re), df_norm(z.im)});
+  return make_double2(c.re, c.im);
+}
+
+__global__ void __launch_bounds__(TS_THREADS)
+update_u_df_kernel(const double* __restrict__ P, const double* __restrict__ V, double* __restrict__ U,
+                   int L, long long rows, const SolverState* __restrict__ st) {
+  __shared__ CDF Ss[CHE];
+  __shared__ CDF al[WD_LMAX * WD_LMAX];
+  if (st->status != ST_OK) return;
+  const CDF z = cdf_of(st->zeta);
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) al[e] = cdf_of(st->alpha[e]);
+  const long long nchunks = (rows + CH - 1) / CH;
+  for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+    const long long r0 = ck * CH;
+    const int nr = (int)min((long long)CH, rows - r0);
+    const int cnt = nr * L;
+    const size_t e0 = (size_t)r0 * L;
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      CDF sv = ldcdf(P, e0 + e);
+      const CDF v = ldcdf(V, e0 + e);
+      cdf_mac(sv, {{-z.re.hi, -z.re.lo}, {-z.im.hi, -z.im.lo}}, v);   // P - zeta V
+      Ss[e] = sv;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int n = e / L, b = e - (e / L) * L;
+      CDF acc = cdf_zero();
+      for (int a = 0; a < L; ++a) cdf_mac(acc, Ss[n * L + a], al[a * L + b]);
+      reinterpret_cast<double2*>(U)[e0 + e] = d2_of(acc);
+    }
+  }
+}
+
+// Long sums (thousands of rows per block): the accumulator is renormalised after every product,
+// so its low word never outgrows ulp(hi) and keeps ~48-bit accuracy.
+WD_DEV void gram_chunk_df(const CDF* As, const CDF* Bs, int rows, int L, CDF& acc) {
+  const int t = threadIdx.x;
+  if (t < L * L) {
+    const int a = t / L, b = t - (t / L) * L;
+    for (int n = 0; n < rows; ++n) {
+      cdf_macj(acc, As[n * L + a], Bs[n * L + b]);
+      acc.re = df_norm(acc.re);
+      acc.im = df_norm(acc.im);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TS_THREADS)
+update_xr_df_kernel(double* __restrict__ X, const double* __restrict__ F, const double* __restrict__ G,
+                    double* __restrict__ R, const double* __restrict__ W, const double* __restrict__ Y,
+                    const double* __restrict__ Rt, int L, long long rows, double2* __restrict__ part,
+                    const SolverState* __restrict__ st) {
+  __shared__ CDF As[CHE], Bs[CHE];
+  __shared__ double nred[CHE];
+  if (st->status != ST_OK) return;
+  const Cx<double> z = sm(st->zeta);
+  CDF acc = cdf_zero();
+  double nacc = 0.0;
+  const long long nchunks = (rows + CH - 1) / CH;
+  for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+    const long long r0 = ck * CH;
+    const int nr = (int)min((long long)CH, rows - r0);
+    const int cnt = nr * L;
+    const size_t e0 = (size_t)r0 * L;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const size_t q = e0 + e;
+      const Cx<double> x = ld2(X, q) + cmul(z, ld2(F, q)) + ld2(G, q);
+      const Cx<double> r = ld2(R, q) - cmul(z, ld2(W, q)) - ld2(Y, q);
+      st2(X, q, x);
+      st2(R, q, r);
+      Bs[e] = cdf_from(r);
+      As[e] = ldcdf(Rt, q);
+      nred[e] = cnorm2(r);
+    }
+    __syncthreads();
+    gram_chunk_df(As, Bs, nr, L, acc);
+    if (threadIdx.x < L)
+      for (int n = 0; n < nr; ++n) nacc += nred[n * L + threadIdx.x];
+    __syncthreads();
+  }
+  double2* p = part + (size_t)blockIdx.x * PART_STRIDE;
+  if (threadIdx.x < L * L) p[threadIdx.x] = d2_of(acc);
+  if (threadIdx.x < L) p[WD_LMAX * WD_LMAX + threadIdx.x] = make_double2(nacc, 0.0);
+}
+
+__global__ void __launch_bounds__(TS_THREADS)
+update_pv_df_kernel(double* __restrict__ P, double* __restrict__ V, const double* __restrict__ R,
+                    const double* __restrict__ W, const double* __restrict__ U,
+                    const double* __restrict__ Y, const double* __restrict__ Rt, int L,
+                    long long rows, double2* __restrict__ part, const SolverState* __restrict__ st) {
+  __shared__ CDF Us[CHE], Ys[CHE], Vs[CHE], Rs[CHE];
+  __shared__ CDF ga[WD_LMAX * WD_LMAX];
+  if (st->status != ST_OK) return;
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) ga[e] = cdf_of(st->gamma[e]);
+  CDF acc = cdf_zero();
+  const long long nchunks = (rows + CH - 1) / CH;
+  for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+    const long long r0 = ck * CH;
+    const int nr = (int)min((long long)CH, rows - r0);
+    const int cnt = nr * L;
+    const size_t e0 = (size_t)r0 * L;
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      Us[e] = ldcdf(U, e0 + e);
+      Ys[e] = ldcdf(Y, e0 + e);
+      Rs[e] = ldcdf(Rt, e0 + e);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int n = e / L, b = e - (e / L) * L;
+      CDF pu = cdf_zero(), py = cdf_zero();
+      for (int a = 0; a < L; ++a) {
+        const CDF gm = ga[a * L + b];
+        cdf_mac(pu, Us[n * L + a], gm);
+        cdf_mac(py, Ys[n * L + a], gm);
+      }
+      const size_t q = e0 + e;
+      const double2 pd = d2_of(pu), yd = d2_of(py);
+      const Cx<double> pv = ld2(R, q) + Cx<double>{pd.x, pd.y};
+      const Cx<double> v = ld2(W, q) + Cx<double>{yd.x, yd.y};
+      st2(P, q, pv);
+      st2(V, q, v);
+      Vs[e] = cdf_from(v);
+    }
+    __syncthreads();
+    gram_chunk_df(Rs, Vs, nr, L, acc);
+  }
+  double2* p = part + (size_t)blockIdx.x * PART_STRIDE;
+  if (threadIdx.x < L * L) p[threadIdx.x] = d2_of(acc);
+}
+
 inline int blocks_for(long long rows) {
   const long long nchunks = (rows + CH - 1) / CH;
   const long long cap = 152LL * 4;
@@ -422,25 +564,36 @@ cudaError_t launch_solve_gamma(SolverState* st, int L, cudaStream_t s) {
 }
 
 cudaError_t launch_update_u(const double* P, const double* V, double* U, int L, long long rows,
-                            const SolverState* st, cudaStream_t s) {
-  update_u_kernel<<<blocks_for(rows), TS_THREADS, 0, s>>>(P, V, U, L, rows, st);
+                            const SolverState* st, cudaStream_t s, bool df) {
+  if (df)
+    update_u_df_kernel<<<blocks_for(rows), TS_THREADS, 0, s>>>(P, V, U, L, rows, st);
+  else
+    update_u_kernel<<<blocks_for(rows), TS_THREADS, 0, s>>>(P, V, U, L, rows, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update_xr(double* X, const double* F, const double* G, double* R,
                              const double* W, const double* Y, const double* Rt, int L,
-                             long long rows, double2* part, SolverState* st, cudaStream_t s) {
+                             long long rows, double2* part, SolverState* st, cudaStream_t s,
+                             bool df) {
   const int nb = blocks_for(rows);
-  update_xr_kernel<<<nb, TS_THREADS, 0, s>>>(X, F, G, R, W, Y, Rt, L, rows, part, st);
+  if (df)
+    update_xr_df_kernel<<<nb, TS_THREADS, 0, s>>>(X, F, G, R, W, Y, Rt, L, rows, part, st);
+  else
+    update_xr_kernel<<<nb, TS_THREADS, 0, s>>>(X, F, G, R, W, Y, Rt, L, rows, part, st);
   finalize_kernel<<<1, WD_LMAX * WD_LMAX, 0, s>>>(part, nb, L, st, GRAM_RTR_NEW, st->rnorm2, false);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update_pv(double* P, double* V, const double* R, const double* W,
                              const double* U, const double* Y, const double* Rt, int L,
-                             long long rows, double2* part, SolverState* st, cudaStream_t s) {
+                             long long rows, double2* part, SolverState* st, cudaStream_t s,
+                             bool df) {
   const int nb = blocks_for(rows);
-  update_pv_kernel<<<nb, TS_THREADS, 0, s>>>(P, V, R, W, U, Y, Rt, L, rows, part, st);
+  if (df)
+    update_pv_df_kernel<<<nb, TS_THREADS, 0, s>>>(P, V, R, W, U, Y, Rt, L, rows, part, st);
+  else
+    update_pv_kernel<<<nb, TS_THREADS, 0, s>>>(P, V, R, W, U, Y, Rt, L, rows, part, st);
   finalize_kernel<<<1, WD_LMAX * WD_LMAX, 0, s>>>(part, nb, L, st, GRAM_RTV, nullptr, false);
   return cudaGetLastError();
 }

@@ -94,3 +94,60 @@ static inline Geom make_geom(const int dims[4]) {
 // (re, im) pairs at 6 + 2*(i*(i-1)/2 + j).  36 reals per block, two blocks (chirality +, -) a site.
 constexpr int CLOV_REALS = 36;
 __host__ __device__ constexpr int tri_index(int i, int j) { return 6 + 2 * (i * (i - 1) / 2 + j); }
+
+// ------------------------------------------------------------------ double-float (FP32 pairs)
+// A value hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits, computed on the FP32 pipes
+// with the error-free transformations of Knuth (two-sum) and Dekker (two-product via FMA).
+struct DF {
+  float hi, lo;
+};
+WD_DEV DF df_from(double d) {
+  const float hi = __double2float_rn(d);
+  return {hi, __double2float_rn(d - (double)hi)};
+}
+WD_DEV double df_to(DF a) { return (double)a.hi + (double)a.lo; }
+// s + e = a + b exactly.  The __f*_rn intrinsics are never contracted into FMAs, which would
+// break the exactness the transformation relies on.
+WD_DEV void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// acc += a * b, accumulator left unnormalised (hi carries the sum, lo gathers the errors)
+WD_DEV void df_mac(DF& acc, DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);      // the rounding error of p, exactly
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float s, t;
+  two_sum(acc.hi, p, s, t);
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
+}
+WD_DEV void df_msub(DF& acc, DF a, DF b) {   // acc -= a * b
+  df_mac(acc, {-a.hi, -a.lo}, b);
+}
+WD_DEV DF df_norm(DF a) {
+  const float s = __fadd_rn(a.hi, a.lo);
+  return {s, __fsub_rn(a.lo, __fsub_rn(s, a.hi))};
+}
+struct CDF {
+  DF re, im;
+};
+WD_DEV CDF cdf_from(Cx<double> z) { return {df_from(z.re), df_from(z.im)}; }
+WD_DEV Cx<double> cdf_to(CDF z) { return {df_to(z.re), df_to(z.im)}; }
+WD_DEV CDF cdf_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+// acc += a * b (complex)
+WD_DEV void cdf_mac(CDF& acc, CDF a, CDF b) {
+  df_mac(acc.re, a.re, b.re);
+  df_msub(acc.re, a.im, b.im);
+  df_mac(acc.im, a.re, b.im);
+  df_mac(acc.im, a.im, b.re);
+}
+// acc += conj(a) * b
+WD_DEV void cdf_macj(CDF& acc, CDF a, CDF b) {
+  df_mac(acc.re, a.re, b.re);
+  df_mac(acc.re, a.im, b.im);
+  df_mac(acc.im, a.re, b.im);
+  df_msub(acc.im, a.im, b.re);
+}

@@ -481,9 +481,13 @@ __global__ void clover_to_cm_kernel(const double* __restrict__ cl, float* __rest
 
 }  // namespace
 
+cudaError_t launch_jacobi_f32_split(const Op& op, const float* g_in, const float* u32, float* g32,
+                                    double* g64, int L, cudaStream_t st);
+
 cudaError_t launch_jacobi_f32_tiled(const Op& op, const float* g_in, const float* u32, float* g32,
                                     double* g64, int L, int rhs_per_thread, int block,
                                     cudaStream_t st) {
+  if (rhs_per_thread == 0) return launch_jacobi_f32_split(op, g_in, u32, g32, g64, L, st);
   if (L % rhs_per_thread != 0 || (block != 64 && block != 128 && block != 256))
     return cudaErrorInvalidValue;
   switch (rhs_per_thread) {
@@ -500,5 +504,99 @@ cudaError_t launch_fp32_operator_copies(const Op& op, cudaStream_t st) {
   const unsigned grid = (unsigned)((op.g.V + threads - 1) / threads);
   links_to_cm_kernel<<<grid, threads, 0, st>>>(op.links, op.links32, op.g.V);
   clover_to_cm_kernel<<<grid, threads, 0, st>>>(op.clov_inv, op.clov_inv32, op.g.V);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FP32 sweep, split stencil
+// The same sweep with the stencil of one (site, rhs) pair split over two warps: in every group of
+// 64 threads, warp 0 takes the x and y hops and warp 1 the z and t hops of the same 32 pairs; the
+// partial sums meet in shared memory, and warp 0 then applies the chirality + block of A_D^{-1}
+// while warp 1 applies the chirality - block.  Twice as many warps cover the same pairs.
+namespace {
+
+template <typename TY>
+__global__ void __launch_bounds__(128)
+jacobi_f32_split_kernel(const float* __restrict__ x, TY* __restrict__ y, const float* __restrict__ u,
+                        const float* __restrict__ links, const float* __restrict__ clov_inv, Geom g,
+                        int L, float kappa) {
+  __shared__ float xch[2][2][12][2][32];   // [group][warp half][component][re/im][lane]
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;       // 0..3
+  const int grp = warp >> 1, half = warp & 1;
+  const long long pair = ((long long)blockIdx.x * 2 + grp) * 32 + lane;
+  const bool valid = pair < (long long)g.V * L;
+  const int s = valid ? (int)(pair / L) : 0;
+  const int r = valid ? (int)(pair - (long long)s * L) : 0;
+  const size_t V = (size_t)g.V;
+  Cx<float> au[2][3], ad[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) { au[a][b] = czero<float>(); ad[a][b] = czero<float>(); }
+  if (valid) {
+    int c[4];
+    site_coords(g, s, c);
+    Cx<float> pu[1][2][3], pd[1][2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) { pu[0][a][b] = czero<float>(); pd[0][a][b] = czero<float>(); }
+    if (half == 0) {
+      hop_cm<0, +1, 1>(x, links, g, s, c, r, L, pu, pd);
+      hop_cm<0, -1, 1>(x, links, g, s, c, r, L, pu, pd);
+      hop_cm<1, +1, 1>(x, links, g, s, c, r, L, pu, pd);
+      hop_cm<1, -1, 1>(x, links, g, s, c, r, L, pu, pd);
+    } else {
+      hop_cm<2, +1, 1>(x, links, g, s, c, r, L, pu, pd);
+      hop_cm<2, -1, 1>(x, links, g, s, c, r, L, pu, pd);
+      hop_cm<3, +1, 1>(x, links, g, s, c, r, L, pu, pd);
+      hop_cm<3, -1, 1>(x, links, g, s, c, r, L, pu, pd);
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) { au[a][b] = pu[0][a][b]; ad[a][b] = pd[0][a][b]; }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    xch[grp][half][k][0][lane] = au[k / 3][k % 3].re;
+    xch[grp][half][k][1][lane] = au[k / 3][k % 3].im;
+    xch[grp][half][6 + k][0][lane] = ad[k / 3][k % 3].re;
+    xch[grp][half][6 + k][1][lane] = ad[k / 3][k % 3].im;
+  }
+  __syncthreads();
+  if (!valid) return;
+  // warp half 0: chirality + (components 0..5); half 1: chirality - (components 6..11)
+  const int ch = half;
+  Cx<float> vin[6], out[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const int k = ch * 6 + i;
+    const Cx<float> hs = {xch[grp][0][k][0][lane] + xch[grp][1][k][0][lane],
+                          xch[grp][0][k][1][lane] + xch[grp][1][k][1][lane]};
+    vin[i] = ldc(u + 2 * (((size_t)k * V + s) * L + r)) + kappa * hs;
+  }
+  herm6s(clov_inv + (size_t)ch * CLOV_REALS * V + s, V, vin, out);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const int k = ch * 6 + i;
+    TY* p = sizeof(TY) == 4 ? y + 2 * (((size_t)k * V + s) * L + r)
+                            : y + 2 * (((size_t)s * 12 + k) * L + r);
+    stc(p, cmake<TY>(TY(out[i].re), TY(out[i].im)));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_jacobi_f32_split(const Op& op, const float* g_in, const float* u32, float* g32,
+                                    double* g64, int L, cudaStream_t st) {
+  const long long pairs = (long long)op.g.V * L;
+  const unsigned grid = (unsigned)((pairs + 63) / 64);   // 64 pairs per 128-thread CTA
+  if (g32)
+    jacobi_f32_split_kernel<float><<<grid, 128, 0, st>>>(g_in, g32, u32, op.links32,
+                                                         op.clov_inv32, op.g, L, (float)op.kappa);
+  else
+    jacobi_f32_split_kernel<double><<<grid, 128, 0, st>>>(g_in, g64, u32, op.links32,
+                                                          op.clov_inv32, op.g, L, (float)op.kappa);
   return cudaGetLastError();
 }

@@ -37,7 +37,8 @@ cudaError_t launch_site_inverse_mixed(const Op& op, const double* u, float* u32,
                                       double* g64, int L, cudaStream_t st);
 
 // FP32 sweep with `rhs_per_thread` (1 or 2; divides L) RHS per thread and `block` threads (64,
-// 128, 256) per CTA; exactly one of g32 / g64 is non-null.
+// 128, 256) per CTA, or -- rhs_per_thread 0 -- the stencil of each pair split over two warps
+// (block 128); exactly one of g32 / g64 is non-null.
 cudaError_t launch_jacobi_f32_tiled(const Op& op, const float* g_in, const float* u32, float* g32,
                                     double* g64, int L, int rhs_per_thread, int block,
                                     cudaStream_t st);
@@ -76,14 +77,17 @@ cudaError_t launch_traces(const double* W, const double* R, int L, long long row
                           double2* part, SolverState* st, cudaStream_t s);
 cudaError_t launch_solve_alpha(SolverState* st, int L, cudaStream_t s);
 cudaError_t launch_solve_gamma(SolverState* st, int L, cudaStream_t s);
+// df: the products with L x L matrices and the Gram products in double-float arithmetic.
 cudaError_t launch_update_u(const double* P, const double* V, double* U, int L, long long rows,
-                            const SolverState* st, cudaStream_t s);
+                            const SolverState* st, cudaStream_t s, bool df);
 cudaError_t launch_update_xr(double* X, const double* F, const double* G, double* R,
                              const double* W, const double* Y, const double* Rt, int L,
-                             long long rows, double2* part, SolverState* st, cudaStream_t s);
+                             long long rows, double2* part, SolverState* st, cudaStream_t s,
+                             bool df);
 cudaError_t launch_update_pv(double* P, double* V, const double* R, const double* W,
                              const double* U, const double* Y, const double* Rt, int L,
-                             long long rows, double2* part, SolverState* st, cudaStream_t s);
+                             long long rows, double2* part, SolverState* st, cudaStream_t s,
+                             bool df);
 
 // ---- abi.cu helpers for other translation units
 struct wd_ctx;
