@@ -133,3 +133,76 @@ def test_solver_mutation_is_caught(kind):
 def test_unmutated_solver_passes_pins():
     assert solver_pin_error(S.__dict__) < 1e-10
     assert invariant_error(S.__dict__) < 1e-10
+
+
+# ---------------------------------------------------------------- network oracle mutations
+from oracle import network as NET
+
+NETWORK_MUTATIONS = {
+    "adjoint_direction_not_swapped": [("return transport(U, lat, phi, d + 4 if d <= 4 else d - 4)",
+                                       "return transport(U, lat, phi, d)")],
+    "gradient_missing_conj": [('G[d, co, c] = np.einsum("vsal,vtal->st", delta[co], np.conj(t))',
+                               'G[d, co, c] = np.einsum("vsal,vtal->st", delta[co], t)')],
+    "adjoint_weight_not_conjugated": [('np.einsum("ts,vtal->vsal", np.conj(W[d, co, c]), delta[co])',
+                                       'np.einsum("ts,vtal->vsal", W[d, co, c], delta[co])')],
+    "backward_transport_wrong_link": [("_dag(U[lat.bwd[mu], mu]), psi[lat.bwd[mu]]",
+                                       "_dag(U[:, mu]), psi[lat.bwd[mu]]")],
+    "loss_not_normalised": [("delta = (diff / (L * en2))[None]", "delta = (diff / L)[None]")],
+    "adam_no_bias_correction": [("mhat = m / (1 - beta1 ** t)", "mhat = m")],
+}
+
+
+def network_pin_error(ns):
+    """Finite-difference gradient pin, gauge covariance and the Adam closed form, as in
+    tests/test_oracle_network.py, on the mutated module."""
+    import test_oracle_network as T
+    errs = []
+    U, lat, W, R, E = T.setup()
+    try:
+        loss, G = ns["loss_and_grad"](U, lat, W, R, E)
+        h = 1e-6
+        rng = np.random.default_rng(1)
+        for li in range(len(W)):
+            for _ in range(6):
+                idx = tuple(rng.integers(0, s) for s in W[li].shape)
+                Wp = [w.copy() for w in W]
+                Wm = [w.copy() for w in W]
+                Wp[li][idx] += h
+                Wm[li][idx] -= h
+                fd = (NET.loss_and_grad(U, lat, Wp, R, E)[0] - NET.loss_and_grad(U, lat, Wm, R, E)[0]) / (2 * h)
+                errs.append(abs(fd - 2 * G[li][idx].real) / max(1.0, abs(fd)))
+        errs.append(abs(loss - NET.loss_and_grad(U, lat, W, R, E)[0]))
+    except Exception:
+        return np.inf
+    dims = (3, 2, 2, 4)
+    Uc = I.random_links(dims, 0.5, seed=4)
+    latc = O.Lattice(dims)
+    Om = I.random_gauge_transform(dims, seed=5)
+    Up = np.empty_like(Uc)
+    for mu in range(4):
+        Up[:, mu] = Om @ Uc[:, mu] @ np.conj(np.swapaxes(Om[latc.fwd[mu]], -1, -2))
+    Wc = I.network_weights(4, 2, seed=3, noise=0.4)
+    psi = I.gaussian_block(dims, 2, seed=6)
+    rot = lambda z: np.einsum("vab,vsbl->vsal", Om, z)
+    a = ns["forward"](Up, latc, Wc, rot(psi))[0]
+    b = rot(ns["forward"](Uc, latc, Wc, psi)[0])
+    errs.append(np.linalg.norm(a - b) / np.linalg.norm(b))
+    Wa, Ga = [np.array([[1.0 + 2.0j]])], [np.array([[0.25 - 1.0j]])]
+    na = ns["adam_step"](Wa, Ga, {}, 0.01, eps=1e-12)[0]
+    errs.append(abs(na[0, 0] - (Wa[0][0, 0] - 0.01 + 0.01j)))
+    return max(errs)
+
+
+# central differences with h = 1e-6 leave ~1e-7 of truncation and rounding in the unmutated
+# check, so the network pins separate mutations at 1e-4 instead of PIN_TOL
+NET_PIN_TOL = 1e-4
+
+
+@pytest.mark.parametrize("kind", sorted(NETWORK_MUTATIONS))
+def test_network_mutation_is_caught(kind):
+    ns = mutated_module(NET, NETWORK_MUTATIONS[kind])
+    assert network_pin_error(ns) > NET_PIN_TOL
+
+
+def test_unmutated_network_passes_pins():
+    assert network_pin_error(NET.__dict__) < 1e-5
