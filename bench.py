@@ -315,6 +315,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: the plain FP64 method (the default); mixed: FP32 Jacobi "
                          "preconditioner with the FP64 outer method")
+    ap.add_argument("--fp32-tile", default="",
+                    help="fix the FP32 sweep tile 'rhs_per_thread,block,min_blocks' instead of "
+                         "autotuning it (reproducible profiling)")
     ap.add_argument("--no-other-form", action="store_true",
                     help="skip timing the other precision form on the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -350,6 +353,8 @@ def main():
     Bh = torch.from_numpy(I.z4_noise(DIMS, L_RHS, seed=source_seed(rank))).pin_memory()
     B = Bh.to(dev)
     ctx = wd.wd_create(links, DIMS, KAPPA, CSW)
+    if args.fp32_tile:
+        wd.wd_set_tile(ctx, L_RHS, *[int(v) for v in args.fp32_tile.split(",")])
     X = torch.zeros_like(B)
     stream = torch.cuda.current_stream(dev)
 

@@ -225,13 +225,15 @@ int wd_profile_reset(wd_ctx* ctx);
 int wd_profile_read(const wd_ctx* ctx, int kernel_class, long long* launches, double* ms);
 const char* wd_profile_name(int kernel_class);
 
-/* Tile of the FP32 Jacobi sweep chosen by the autotuner for this L (RHS per thread, threads per
- * CTA).  The autotuner times every candidate tile once, at the first FP32 preconditioner call with
- * a given L, and keeps the fastest in the context.  WD_EINVAL until then. */
-int wd_tuned_tile(const wd_ctx* ctx, int L, int* rhs_per_thread, int* block);
-/* Sets that tile by hand instead: rhs_per_thread 1 or 2 dividing L with block 64, 128 or 256, or
- * rhs_per_thread 0 with block 128 -- the stencil of every (site, rhs) pair split over two warps. */
-int wd_set_tile(wd_ctx* ctx, int L, int rhs_per_thread, int block);
+/* Tile of the FP32 Jacobi sweep chosen by the autotuner for this L: RHS per thread, threads per
+ * CTA, and the minimum resident CTAs per SM the kernel was compiled for (0: none; 8: at most 128
+ * registers a thread).  The autotuner times every candidate tile once, at the first FP32
+ * preconditioner call with a given L, and keeps the fastest in the context.  WD_EINVAL until then. */
+int wd_tuned_tile(const wd_ctx* ctx, int L, int* rhs_per_thread, int* block, int* min_blocks);
+/* Sets that tile by hand instead: rhs_per_thread 1 or 2 dividing L with block 64, 128 or 256 and
+ * min_blocks 0 (or 8 with block 64), or rhs_per_thread 0 with block 128 -- the stencil of every
+ * (site, rhs) pair split over two warps. */
+int wd_set_tile(wd_ctx* ctx, int L, int rhs_per_thread, int block, int min_blocks);
 
 /* Lattice size and parameters of a context (for bindings): dims[4], V, kappa, c_SW. */
 int wd_query(const wd_ctx* ctx, int dims[4], long long* volume, double* kappa, double* csw);

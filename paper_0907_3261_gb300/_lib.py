@@ -101,9 +101,9 @@ def lib():
     L.wd_profile_enable.argtypes = [vp, i]
     L.wd_profile_reset.argtypes = [vp]
     L.wd_profile_read.argtypes = [vp, i, C.POINTER(C.c_longlong), C.POINTER(d)]
-    L.wd_tuned_tile.argtypes = [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.wd_tuned_tile.argtypes = [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.wd_tuned_tile.restype = C.c_int
-    L.wd_set_tile.argtypes = [vp, i, i, i]
+    L.wd_set_tile.argtypes = [vp, i, i, i, i]
     L.wd_set_tile.restype = C.c_int
     L.wd_profile_name.argtypes = [i]
     L.wd_profile_name.restype = C.c_char_p
@@ -301,16 +301,16 @@ def wd_profile_read(ctx: Context) -> dict:
 
 
 def wd_tuned_tile(ctx: Context, L: int):
-    """(RHS per thread, threads per CTA) the autotuner chose for the FP32 sweep, or None."""
-    r, b = C.c_int(), C.c_int()
-    if lib().wd_tuned_tile(ctx.handle, int(L), C.byref(r), C.byref(b)) != WD_OK:
+    """(RHS per thread, threads per CTA, min CTAs per SM) of the FP32 sweep for L, or None."""
+    r, b, m = C.c_int(), C.c_int(), C.c_int()
+    if lib().wd_tuned_tile(ctx.handle, int(L), C.byref(r), C.byref(b), C.byref(m)) != WD_OK:
         return None
-    return int(r.value), int(b.value)
+    return int(r.value), int(b.value), int(m.value)
 
 
-def wd_set_tile(ctx: Context, L: int, rhs_per_thread: int, block: int) -> None:
+def wd_set_tile(ctx: Context, L: int, rhs_per_thread: int, block: int, min_blocks: int = 0) -> None:
     """Fix the FP32 sweep's tile for this L instead of autotuning it."""
-    _check(lib().wd_set_tile(ctx.handle, int(L), int(rhs_per_thread), int(block)))
+    _check(lib().wd_set_tile(ctx.handle, int(L), int(rhs_per_thread), int(block), int(min_blocks)))
 
 
 

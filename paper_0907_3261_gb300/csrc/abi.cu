@@ -120,6 +120,7 @@ struct wd_ctx {
   // autotuned tile of the FP32 sweep per L: RHS per thread and threads per CTA (0 = not tuned)
   int tile_r[WD_LMAX + 1] = {};
   int tile_block[WD_LMAX + 1] = {};
+  int tile_minb[WD_LMAX + 1] = {};
   bool tile_set[WD_LMAX + 1] = {};
   wd_net* active_net = nullptr;   // learned preconditioner of the running solve (mode 2)
   // device-controlled (graph) solves
@@ -220,7 +221,8 @@ int ensure_workspace(wd_ctx* c, int L) {
 // Picks the FP32 sweep's tile (RHS per thread, threads per CTA) for this lattice and L by timing
 // every candidate on the context's FP32 blocks (zeroed first); the winner is kept in the context.
 int autotune_f32(wd_ctx* c, int L, cudaStream_t s) {
-  static const int cand[][2] = {{1, 64}, {1, 128}, {1, 256}, {2, 64}, {2, 128}, {2, 256}, {0, 128}};
+  static const int cand[][3] = {{1, 64, 0}, {1, 128, 0}, {1, 256, 0}, {2, 64, 0}, {2, 128, 0},
+                                {2, 256, 0}, {0, 128, 0}, {2, 64, 8}};
   const size_t bytes = (size_t)c->op.g.V * 12 * L * 8;
   float* u32 = static_cast<float*>(c->blk32[0].p);
   float* a = static_cast<float*>(c->blk32[1].p);
@@ -235,10 +237,10 @@ int autotune_f32(wd_ctx* c, int L, cudaStream_t s) {
   cudaError_t err = cudaSuccess;
   for (int i = 0; i < (int)(sizeof(cand) / sizeof(cand[0])) && err == cudaSuccess; ++i) {
     if (cand[i][0] > 0 && L % cand[i][0] != 0) continue;
-    err = launch_jacobi_f32_tiled(c->op, a, u32, b, nullptr, L, cand[i][0], cand[i][1], s);
+    err = launch_jacobi_f32_tiled(c->op, a, u32, b, nullptr, L, cand[i][0], cand[i][1], cand[i][2], s);
     if (err == cudaSuccess) err = cudaEventRecord(e0, s);
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
-      err = launch_jacobi_f32_tiled(c->op, a, u32, b, nullptr, L, cand[i][0], cand[i][1], s);
+      err = launch_jacobi_f32_tiled(c->op, a, u32, b, nullptr, L, cand[i][0], cand[i][1], cand[i][2], s);
     if (err == cudaSuccess) err = cudaEventRecord(e1, s);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -250,6 +252,7 @@ int autotune_f32(wd_ctx* c, int L, cudaStream_t s) {
   CU(err);
   c->tile_r[L] = cand[best_i][0];
   c->tile_block[L] = cand[best_i][1];
+  c->tile_minb[L] = cand[best_i][2];
   c->tile_set[L] = true;
   return WD_OK;
 }
@@ -308,7 +311,7 @@ int precondition(wd_ctx* c, const double* R, double* a, double* b, double** res,
       const bool last = i == j - 1;
       LAUNCH(WD_K_JACOBI, 1,
              launch_jacobi_f32_tiled(op, cur, u32, last ? nullptr : nxt, last ? a : nullptr, L,
-                                     c->tile_r[L], c->tile_block[L], s));
+                                     c->tile_r[L], c->tile_block[L], c->tile_minb[L], s));
       if (hop_count) ++*hop_count;
       float* t = cur;
       cur = nxt;
@@ -488,7 +491,10 @@ void wd_destroy(wd_ctx* c) {
   cudaFree(c->op.clov_inv32);
   for (auto& b : c->blk) b.release();
   for (auto& b : c->blk32) b.release();
-  for (int l = 0; l <= WD_LMAX; ++l) { c->tile_r[l] = c->tile_block[l] = 0; c->tile_set[l] = false; }
+  for (int l = 0; l <= WD_LMAX; ++l) {
+    c->tile_r[l] = c->tile_block[l] = c->tile_minb[l] = 0;
+    c->tile_set[l] = false;
+  }
   c->part.release();
   c->stage_in.release();
   c->stage_out.release();
@@ -587,25 +593,29 @@ const char* wd_profile_name(int cls) {
   return (cls >= 0 && cls < WD_K_COUNT) ? names[cls] : "unknown";
 }
 
-int wd_set_tile(wd_ctx* c, int L, int rhs_per_thread, int block) {
+int wd_set_tile(wd_ctx* c, int L, int rhs_per_thread, int block, int min_blocks) {
   if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
   CHECK(check_L(L));
-  const bool split = rhs_per_thread == 0 && block == 128;
+  const bool split = rhs_per_thread == 0 && block == 128 && min_blocks == 0;
+  const bool capped = min_blocks == 8 && block == 64 && rhs_per_thread != 0;
   if (!split && ((rhs_per_thread != 1 && rhs_per_thread != 2) || L % rhs_per_thread != 0 ||
-                 (block != 64 && block != 128 && block != 256))) {
-    set_err("tile (%d RHS/thread, %d threads) not available for L = %d", rhs_per_thread, block, L);
+                 (block != 64 && block != 128 && block != 256) || (min_blocks != 0 && !capped))) {
+    set_err("tile (%d RHS/thread, %d threads, min %d blocks) not available for L = %d",
+            rhs_per_thread, block, min_blocks, L);
     return WD_EINVAL;
   }
   c->tile_r[L] = rhs_per_thread;
   c->tile_block[L] = block;
+  c->tile_minb[L] = min_blocks;
   c->tile_set[L] = true;
   return WD_OK;
 }
 
-int wd_tuned_tile(const wd_ctx* c, int L, int* rhs_per_thread, int* block) {
+int wd_tuned_tile(const wd_ctx* c, int L, int* rhs_per_thread, int* block, int* min_blocks) {
   if (!c || L < 1 || L > WD_LMAX || !c->tile_set[L]) { set_err("no tuned tile for this L"); return WD_EINVAL; }
   if (rhs_per_thread) *rhs_per_thread = c->tile_r[L];
   if (block) *block = c->tile_block[L];
+  if (min_blocks) *min_blocks = c->tile_minb[L];
   return WD_OK;
 }
 

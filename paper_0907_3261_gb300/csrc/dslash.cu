@@ -394,8 +394,8 @@ WD_DEV void hop_cm(const float* __restrict__ x, const float* __restrict__ links,
   }
 }
 
-template <int R, typename TY>
-__global__ void __launch_bounds__(256)
+template <int R, typename TY, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
 jacobi_f32_kernel(const float* __restrict__ x, TY* __restrict__ y, const float* __restrict__ u,
                   const float* __restrict__ links, const float* __restrict__ clov_inv, Geom g,
                   int L, float kappa) {
@@ -452,10 +452,15 @@ jacobi_f32_kernel(const float* __restrict__ x, TY* __restrict__ y, const float* 
 
 template <int R, typename TY>
 cudaError_t launch_jacobi_f32_r(const Op& op, const float* g_in, const float* u32, TY* out, int L,
-                                int block, cudaStream_t st) {
+                                int block, int min_blocks, cudaStream_t st) {
   const long long n = (long long)op.g.V * (L / R);
-  jacobi_f32_kernel<R, TY><<<(unsigned)((n + block - 1) / block), block, 0, st>>>(
-      g_in, out, u32, op.links32, op.clov_inv32, op.g, L, (float)op.kappa);
+  const unsigned grid = (unsigned)((n + block - 1) / block);
+  if (min_blocks == 8 && block == 64)    // at most 128 registers: 16 warps per SM
+    jacobi_f32_kernel<R, TY, 64, 8><<<grid, block, 0, st>>>(
+        g_in, out, u32, op.links32, op.clov_inv32, op.g, L, (float)op.kappa);
+  else
+    jacobi_f32_kernel<R, TY, 256, 1><<<grid, block, 0, st>>>(
+        g_in, out, u32, op.links32, op.clov_inv32, op.g, L, (float)op.kappa);
   return cudaGetLastError();
 }
 
@@ -486,15 +491,15 @@ cudaError_t launch_jacobi_f32_split(const Op& op, const float* g_in, const float
 
 cudaError_t launch_jacobi_f32_tiled(const Op& op, const float* g_in, const float* u32, float* g32,
                                     double* g64, int L, int rhs_per_thread, int block,
-                                    cudaStream_t st) {
+                                    int min_blocks, cudaStream_t st) {
   if (rhs_per_thread == 0) return launch_jacobi_f32_split(op, g_in, u32, g32, g64, L, st);
   if (L % rhs_per_thread != 0 || (block != 64 && block != 128 && block != 256))
     return cudaErrorInvalidValue;
   switch (rhs_per_thread) {
-    case 1: return g32 ? launch_jacobi_f32_r<1>(op, g_in, u32, g32, L, block, st)
-                       : launch_jacobi_f32_r<1>(op, g_in, u32, g64, L, block, st);
-    case 2: return g32 ? launch_jacobi_f32_r<2>(op, g_in, u32, g32, L, block, st)
-                       : launch_jacobi_f32_r<2>(op, g_in, u32, g64, L, block, st);
+    case 1: return g32 ? launch_jacobi_f32_r<1>(op, g_in, u32, g32, L, block, min_blocks, st)
+                       : launch_jacobi_f32_r<1>(op, g_in, u32, g64, L, block, min_blocks, st);
+    case 2: return g32 ? launch_jacobi_f32_r<2>(op, g_in, u32, g32, L, block, min_blocks, st)
+                       : launch_jacobi_f32_r<2>(op, g_in, u32, g64, L, block, min_blocks, st);
     default: return cudaErrorInvalidValue;
   }
 }

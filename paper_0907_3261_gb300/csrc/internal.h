@@ -37,11 +37,12 @@ cudaError_t launch_site_inverse_mixed(const Op& op, const double* u, float* u32,
                                       double* g64, int L, cudaStream_t st);
 
 // FP32 sweep with `rhs_per_thread` (1 or 2; divides L) RHS per thread and `block` threads (64,
-// 128, 256) per CTA, or -- rhs_per_thread 0 -- the stencil of each pair split over two warps
-// (block 128); exactly one of g32 / g64 is non-null.
+// 128, 256) per CTA -- with min_blocks 8 and block 64 compiled for at most 128 registers -- or,
+// rhs_per_thread 0, the stencil of each pair split over two warps (block 128); exactly one of
+// g32 / g64 is non-null.
 cudaError_t launch_jacobi_f32_tiled(const Op& op, const float* g_in, const float* u32, float* g32,
                                     double* g64, int L, int rhs_per_thread, int block,
-                                    cudaStream_t st);
+                                    int min_blocks, cudaStream_t st);
 
 // ---- clover.cu
 // Builds clov and clov_inv from links; *singular_dev receives 1 if some 6x6 block is singular.
