@@ -6,10 +6,10 @@ Workload (the paper's lattice, Sec. 3.1, with synthetic links in place of its co
 Z4-noise sources (seed 1 + rank), Jacobi j = 12 (the paper's recommended L = 12, j >= 12, Sec. 3.3),
 X_0 = 0, R~_0 = R_0, tolerance 1e-12 on the recursive residual and then on the true residual.
 One step = one complete solve through the C-ABI, by default the plain FP64 method (--precision
-mixed: FP32 Jacobi preconditioner with the FP64 outer method); the run also times the other form
-on the same workload for comparison.  kappa = 0.134 is the largest value of the
-0.001-step sweep from 0.115 at which the L = 1, j = 0 solve still converges (660 iterations);
-at 0.135 it no longer does.
+mixed: FP32 Jacobi preconditioner with the FP64 outer method; bf16: the same sweeps on BF16-stored
+blocks); the run also times the other forms on the same workload for comparison.  kappa = 0.134
+is the largest value of the 0.001-step sweep from 0.115 at which the L = 1, j = 0 solve still
+converges (660 iterations); at 0.135 it no longer does.
 
 Prints one JSON line on stdout.  --impl reference times the FP64 oracle on the host cores instead.
 With torchrun each rank solves its own sources (independent problems, no collective on the data
@@ -42,17 +42,31 @@ TOL = 1e-12
 # by the reference arm, which cannot run the full oracle solve, to scale its per-MVM time.
 WORKLOAD_ITERS = 36
 
+PRECISIONS = {"fp64": 0, "mixed": 1, "bf16": 3, "df": 4}   # bbicggr_opts.precision of each form
+FORM_NAMES = {"fp64": "plain FP64 Jacobi", "mixed": "mixed: FP32 Jacobi preconditioner",
+              "bf16": "mixed: Jacobi preconditioner on BF16-stored blocks",
+              "df": "mixed: double-float Jacobi preconditioner (FP32 pairs, FP32 operator)"}
+# FP32 instructions per site and RHS of one double-float sweep: 8 hops x (12 two-sum additions
+# for the projection, 72 split products for the link, 24 additions into the sums) + the two 6x6
+# blocks (264 split products) + U + kappa H (24) + normalising the 24 stored reals (3 each) + the
+# row-2 rebuild of 8 links (30 each), with 11 instructions per split product and 8 per addition.
+DF_OPS = 8 * (12 * 8 + 72 * 11 + 24 * 8) + 264 * 11 + 24 * 11 + 24 * 3 + 8 * 30
+FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12   # FP32 lane instructions per second (2070 MHz)
 METRIC = "time-to-solution at true resid 1e-12 for L RHS; Dslash HBM GB/s vs peak"
 FLOP_APPLY = 1824          # flop per site per RHS of A (1320 hopping + 504 clover)
 FLOP_JACOBI = 1872         # flop per site per RHS of one Jacobi sweep A_D^{-1}(U + kappa H G)
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
 
 
-def algorithmic_bytes(kind: str, L: int, real_bytes: int = 8) -> int:
-    """Minimum DRAM bytes per site: 4 links (each link serves two sites), one packed 2x(6x6)
-    clover or inverse block, and the spinors read or written once."""
-    links = 4 * 18 * real_bytes
-    clov = 72 * real_bytes
+def algorithmic_bytes(kind: str, L: int, real_bytes: int = 8, link_reals: int = 18,
+                      op_real_bytes: int = 0) -> int:
+    """Minimum DRAM bytes per site: 4 links of `link_reals` reals (each link serves two sites),
+    one packed 2x(6x6) clover or inverse block, and the spinors (reals of `real_bytes`) read or
+    written once.  The links and clover blocks have reals of `op_real_bytes` (default: as the
+    spinors)."""
+    op_real_bytes = op_real_bytes or real_bytes
+    links = 4 * link_reals * op_real_bytes
+    clov = 72 * op_real_bytes
     spinor = 24 * real_bytes * L
     if kind == "dslash_apply":
         return links + clov + 2 * spinor
@@ -312,14 +326,19 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS),
                     help="fp64: the plain FP64 method (the default); mixed: FP32 Jacobi "
-                         "preconditioner with the FP64 outer method")
+                         "preconditioner with the FP64 outer method; bf16: the preconditioner's "
+                         "blocks stored in BF16, FP32 arithmetic; df: double-float (FP32-pair) "
+                         "preconditioner arithmetic")
     ap.add_argument("--fp32-tile", default="",
-                    help="fix the FP32 sweep tile 'rhs_per_thread,block,min_blocks' instead of "
+                    help="fix the FP32 sweep tile 'rhs_per_thread,block,min_blocks[,staged]' instead of "
                          "autotuning it (reproducible profiling)")
+    ap.add_argument("--bf16-tile", default="", help="the same for the BF16-storage sweep")
+    ap.add_argument("--link-reals", type=int, default=0, choices=[0, 12, 18],
+                    help="link format of the low-precision sweeps (0: the library's choice)")
     ap.add_argument("--no-other-form", action="store_true",
-                    help="skip timing the other precision form on the same workload")
+                    help="skip timing the other precision forms on the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="tts", choices=["tts", "batch24"],
                     help="tts: the time-to-solution line; batch24: 24 solves in one CUDA graph")
@@ -347,14 +366,19 @@ def main():
         dist.barrier()
     import paper_0907_3261_gb300 as wd
     from paper_0907_3261_gb300 import inputs as I
-    prec = {"fp64": 0, "mixed": 1}[args.precision]
+    prec = PRECISIONS[args.precision]
 
     links = torch.from_numpy(I.random_links(DIMS, LINK_EPS, seed=0)).to(dev)
     Bh = torch.from_numpy(I.z4_noise(DIMS, L_RHS, seed=source_seed(rank))).pin_memory()
     B = Bh.to(dev)
     ctx = wd.wd_create(links, DIMS, KAPPA, CSW)
     if args.fp32_tile:
-        wd.wd_set_tile(ctx, L_RHS, *[int(v) for v in args.fp32_tile.split(",")])
+        wd.wd_set_tile(ctx, L_RHS, *[int(v) for v in args.fp32_tile.split(",")], precision=1)
+    if args.bf16_tile:
+        wd.wd_set_tile(ctx, L_RHS, *[int(v) for v in args.bf16_tile.split(",")], precision=3)
+    if args.link_reals:
+        wd.wd_set_link_reals(ctx, args.link_reals)
+    link_reals = wd.wd_link_reals(ctx)
     X = torch.zeros_like(B)
     stream = torch.cuda.current_stream(dev)
 
@@ -404,10 +428,11 @@ def main():
     e2e_s = maxr((time.perf_counter() - t0) / args.steps)
     block = B.numel() * 16
 
-    # ---- the other precision form on the same workload, for comparison (not the value)
-    other = None
-    if not args.no_other_form:
-        oprec = 1 if prec == 0 else 0
+    # ---- the other precision forms on the same workload, for comparison (not the value)
+    others = []
+    for oname, oprec in ([] if args.no_other_form else list(PRECISIONS.items())):
+        if oprec == prec:
+            continue
 
         def solve_other():
             X.zero_()
@@ -424,11 +449,11 @@ def main():
         torch.cuda.synchronize(dev)
         to = maxr(f0.elapsed_time(f1) / 2 / 1e3)
         ok = ok and all(i["status"] == wd.WD_OK for i in io)
-        other = {"form": "mixed: FP32 Jacobi preconditioner" if oprec else "plain FP64 Jacobi",
-                 "value": round(to, 6), "unit": "s", "iters": io[-1]["iters"],
-                 "fallbacks": io[-1]["fallbacks"],
-                 "max_true_resid": max(i["max_true_resid"] for i in io),
-                 "ratio_to_value": round(to / (ms_step / 1e3), 3)}
+        others.append({"form": FORM_NAMES[oname], "precision": oname,
+                       "value": round(to, 6), "unit": "s", "iters": io[-1]["iters"],
+                       "fallbacks": io[-1]["fallbacks"],
+                       "max_true_resid": max(i["max_true_resid"] for i in io),
+                       "ratio_to_value": round(to / (ms_step / 1e3), 3)})
 
     # ---- roofline of the dominant kernel class, and of every stencil class
     V = int(np.prod(DIMS))
@@ -438,19 +463,34 @@ def main():
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    fp32_sweeps = args.precision == "mixed"
+    sweep_prec = {"fp64": "fp64", "mixed": "fp32", "bf16": "bf16", "df": "df"}[args.precision]
     per_kernel = {}
-    for cls in ("dslash_jacobi", "dslash_apply"):
+    for cls in ("dslash_jacobi_lp", "dslash_jacobi", "dslash_apply"):
         n, ms = prof.get(cls, (0, 0.0))
         if not n:
             continue
         avg_s = ms / n / 1e3
-        f32 = cls == "dslash_jacobi" and fp32_sweeps
-        flop_unit = FLOP_JACOBI if cls == "dslash_jacobi" else FLOP_APPLY
-        nbytes = algorithmic_bytes(cls, L_RHS, 4 if f32 else 8) * V
+        kprec = sweep_prec if cls == "dslash_jacobi_lp" else "fp64"
+        f32 = kprec in ("fp32", "bf16")
+        flop_unit = FLOP_APPLY if cls == "dslash_apply" else FLOP_JACOBI
+        kind = "dslash_apply" if cls == "dslash_apply" else "dslash_jacobi"
+        if f32:   # spinors FP32 or BF16; links and A_D^{-1} FP32
+            nbytes = algorithmic_bytes(kind, L_RHS, 4 if kprec == "fp32" else 2, link_reals, 4) * V
+        elif kprec == "df":   # spinors as FP32 pairs; links and A_D^{-1} FP32
+            nbytes = algorithmic_bytes(kind, L_RHS, 8, link_reals, 4) * V
+        else:
+            nbytes = algorithmic_bytes(kind, L_RHS, 8) * V
         tflops = flop_unit * V * L_RHS / avg_s / 1e12
         gbs = nbytes / avg_s / 1e9
-        if f32:
+        if kprec == "df":
+            tops = DF_OPS * V * L_RHS / avg_s / 1e12
+            fig = {"bound": "alu", "achieved": round(tops, 3), "peak": round(FP32_PEAK_TOPS, 2),
+                   "unit": "T FP32 instructions/s", "frac": round(tops / FP32_PEAK_TOPS, 4),
+                   "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                   "fp32_ops_per_site_rhs": DF_OPS, "tflops_fp64_equivalent": round(tflops, 3),
+                   "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                           "frac": round(gbs / hbm_peak, 4)}}
+        elif f32:
             fig = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                    "frac": round(gbs / hbm_peak, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                    "tflops_fp32": round(tflops, 3)}
@@ -461,8 +501,8 @@ def main():
                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                    "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                            "frac": round(gbs / hbm_peak, 4)}}
-        fig.update({"kernel": cls, "precision": "fp32" if f32 else "fp64",
-                    "traffic": ncu_traffic(cls, "fp32" if f32 else "fp64"),
+        fig.update({"kernel": cls, "precision": kprec,
+                    "traffic": ncu_traffic(cls, kprec),
                     "algorithmic_bytes_per_launch": nbytes, "flop_per_site_rhs": flop_unit,
                     "avg_launch_ms": round(avg_s * 1e3, 4), "launches": n,
                     "total_ms": round(ms, 2)})
@@ -472,12 +512,14 @@ def main():
     roofline["stencil_kernels"] = per_kernel
 
     launches = sum(n for k, (n, _) in prof.items())
-    tile = wd.wd_tuned_tile(ctx, L_RHS)
+    tile = wd.wd_tuned_tile(ctx, L_RHS, precision=3 if prec == 3 else 1) if prec in (1, 2, 3) else None
     out = {"metric": METRIC, "value": round(ms_step / 1e3, 6), "unit": "s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if prec == 0 else "f64+f32", "data": "synthetic",
-           "config": dict(config(args), fp32_sweep_tile=tile), "roofline": roofline,
+           "dtype": {0: "f64", 1: "f64+f32", 3: "f64+f32(bf16 storage)", 4: "f64+df32x2"}[prec],
+           "data": "synthetic",
+           "config": dict(config(args), sweep_tile=tile, link_reals=link_reals),
+           "roofline": roofline,
            "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": 2 * block,
                    "d2h_bytes_per_step": block},
            "gpu_launches": launches, "clocks": clocks,
@@ -487,12 +529,13 @@ def main():
                      "restarts": infos[-1]["restarts"],
                      "fallbacks": infos[-1]["fallbacks"]},
            "kernels": {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in prof.items() if n or ms}}
-    if other is not None:
-        out["other_form"] = other
+    if others:
+        out["other_forms"] = others
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_apply, t_inv, cores = oracle_sample(L_RHS)
         # the oracle runs the plain FP64 method: scale by that method's iteration count
-        k = infos[-1]["iters"] if prec == 0 or other is None else other["iters"]
+        k = infos[-1]["iters"] if prec == 0 else next(
+            (o["iters"] for o in others if o["precision"] == "fp64"), infos[-1]["iters"])
         out["cpu_baseline"] = {
             "value": round(oracle_tts(k, J_JACOBI, t_apply, t_inv), 3), "unit": "s",
             "cores": cores, "kind": "oracle",

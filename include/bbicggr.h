@@ -68,16 +68,20 @@ typedef struct {
                              FP64; 2: as 1, and the direction recurrences U = (P - zeta V) alpha,
                              P = R + U gamma, V = W + Y gamma and the Gram products in double-float
                              (FP32-pair, ~48-bit) arithmetic on the FP32 pipes, with the X and R
-                             updates and column norms still FP64 */
+                             updates and column norms still FP64; 3: as 1 with the
+                             preconditioner's blocks (its copy of U and the sweep iterates) stored
+                             in BF16, arithmetic FP32.  In 1-3 the sweeps read 12-real links
+                             (rows 0 and 1, row 2 rebuilt) when wd_link_reals says 12 */
   double* history;        /* optional host array: max_i ||r_i||/||b_i|| after every R update */
   int history_len;        /* capacity of history (entries beyond it are dropped) */
-  int stall_window;       /* precision 1 only: when the max relative residual has not reached a new
-                             minimum for this many iterations, or the FP32-preconditioned run breaks
+  int stall_window;       /* precision 1-3 only: when the max relative residual has not reached a new
+                             minimum for this many iterations, or the low-precision run breaks
                              down or diverges, the solve starts over from X_0 with the FP64
-                             preconditioner (block BiCGGR needs a fixed linear M, and FP32
-                             rounding of M can stall it near the critical kappa).  Default 16;
+                             preconditioner (block BiCGGR needs a fixed linear M, and the
+                             rounding of a low-precision M can stall it near the critical kappa).  Default 16;
                              0 disables the fallback.  Costs one more N x L block of workspace */
-  wd_net* net;            /* not NULL: M is this learned network (FP32) instead of j-step Jacobi;
+  wd_net* net;            /* not NULL: M is this learned network instead of j-step Jacobi, with
+                             its activations in FP32, or in BF16 with precision 3;
                              the stall rule above applies and its fallback is FP64 Jacobi with the
                              solve's j.  mvm_paper then counts the products with A only */
 } bbicggr_opts;
@@ -96,7 +100,7 @@ typedef struct {
   double* true_resid;     /* [L] or NULL */
   int history_count;      /* entries written to opts->history */
   double seconds;         /* wall time of the call (host clock, includes host<->device copies) */
-  int fallbacks;          /* switches from the FP32 to the FP64 preconditioner (0 or 1) */
+  int fallbacks;          /* switches from the low-precision to the FP64 preconditioner (0 or 1) */
 } bbicggr_info;
 
 /* Build the operator A for the given links (Sec. 2; kappa and c_SW as in Sec. 3.1).
@@ -115,8 +119,9 @@ int wd_apply(wd_ctx* ctx, const void* X, void* Y, int L, void* stream);
 
 /* G = M R, the j-step Jacobi preconditioner of Sec. 2 from the zero initial guess (Sec. 3.3):
  * G = sum_{i<j} (I - A_D^{-1} A)^i A_D^{-1} R for j >= 1 and G = R for j = 0.  Computed as j sweeps
- * G <- A_D^{-1}(R + kappa H G), H the hopping term.  `precision` as in bbicggr_opts (0 = FP64,
- * 1 = FP32 sweeps).  R and G must not overlap. */
+ * G <- A_D^{-1}(R + kappa H G), H the hopping term.  `precision`: 0 = FP64 sweeps, 1 = FP32
+ * sweeps, 3 = FP32 arithmetic on BF16-stored blocks (as in bbicggr_opts).  R and G must not
+ * overlap. */
 int jacobi_precond(wd_ctx* ctx, const void* R, void* G, int L, int j, int precision, void* stream);
 
 /* jacobi_precond_noalloc: the same G = M R as jacobi_precond (FP64 sweeps), computed without
@@ -181,15 +186,17 @@ const char* wd_last_error(void);
  *   (T_{1+mu} psi)(x) = U_mu(x) psi(x+mu),  (T_{5+mu} psi)(x) = U_mu(x-mu)^H psi(x-mu),
  * W[d][c'][c] a complex 4x4 spin matrix.  Weights at the ABI: complex128, per layer
  * [9][C_out][C_in][4][4], layers concatenated (wd_net_num_weights complex numbers); stored as
- * complex64.  Activations FP32.  Training: loss = (1/L) sum_i ||N(r_i) - e_i||^2 / ||e_i||^2 over
+ * complex64.  Activations FP32; inference may store them in BF16 instead (FP32 arithmetic either
+ * way).  Training: loss = (1/L) sum_i ||N(r_i) - e_i||^2 / ||e_i||^2 over
  * pairs (r_i, e_i = A^{-1} r_i), gradient d loss / d conj(W), Adam on (Re W, Im W). */
 int wd_net_create(wd_net** out, int layers, int hidden, const void* weights /* host or device */);
 void wd_net_destroy(wd_net* net);
 long long wd_net_num_weights(const wd_net* net);
 int wd_net_set_weights(wd_net* net, const void* weights);   /* also resets the Adam state */
 int wd_net_get_weights(const wd_net* net, void* out);       /* host or device, complex128 */
-/* G = N(R) for device blocks R, G (N x L, complex128, site-major). */
-int wd_net_apply(wd_ctx* ctx, wd_net* net, const void* R, void* G, int L, void* stream);
+/* G = N(R) for device blocks R, G (N x L, complex128, site-major); bf16 = 1 stores the
+ * activations in BF16 (0: FP32). */
+int wd_net_apply(wd_ctx* ctx, wd_net* net, const void* R, void* G, int L, int bf16, void* stream);
 /* Forward and backward pass on device blocks R, E: *loss (host, may be NULL) and the gradient
  * d loss / d conj(W), kept in the network for wd_net_adam_step and copied to `grad` (complex128,
  * host or device, may be NULL).  Synchronises the stream. */
@@ -206,7 +213,7 @@ int wd_net_adam_step(wd_net* net, double lr, void* stream);
 enum {
   WD_K_APPLY = 0,      /* dslash Y = A X */
   WD_K_RESID,          /* dslash R = B - A X */
-  WD_K_JACOBI,         /* dslash Jacobi sweep G <- A_D^{-1}(U + kappa H G) */
+  WD_K_JACOBI,         /* FP64 Jacobi sweep G <- A_D^{-1}(U + kappa H G) */
   WD_K_SITE_INV,       /* first Jacobi sweep G = A_D^{-1} U */
   WD_K_UPDATE_U,       /* U = (P - zeta V) alpha */
   WD_K_UPDATE_XR,      /* X += zeta F + G, R -= zeta W + Y, R~_0^H R, ||r_i||^2 */
@@ -218,6 +225,8 @@ enum {
   WD_K_COPY,           /* device-to-device block copies */
   WD_K_CONVERT,        /* FP64 <-> FP32 conversions of the FP32 preconditioner */
   WD_K_NET,            /* learned preconditioner G = N(R) (all its kernels) */
+  WD_K_JACOBI_LP,      /* Jacobi sweep in FP32 arithmetic on FP32 or BF16 blocks, or in
+                          double-float arithmetic */
   WD_K_COUNT
 };
 int wd_profile_enable(wd_ctx* ctx, int timing_on);
@@ -225,15 +234,29 @@ int wd_profile_reset(wd_ctx* ctx);
 int wd_profile_read(const wd_ctx* ctx, int kernel_class, long long* launches, double* ms);
 const char* wd_profile_name(int kernel_class);
 
-/* Tile of the FP32 Jacobi sweep chosen by the autotuner for this L: RHS per thread, threads per
- * CTA, and the minimum resident CTAs per SM the kernel was compiled for (0: none; 8: at most 128
- * registers a thread).  The autotuner times every candidate tile once, at the first FP32
- * preconditioner call with a given L, and keeps the fastest in the context.  WD_EINVAL until then. */
-int wd_tuned_tile(const wd_ctx* ctx, int L, int* rhs_per_thread, int* block, int* min_blocks);
-/* Sets that tile by hand instead: rhs_per_thread 1 or 2 dividing L with block 64, 128 or 256 and
- * min_blocks 0 (or 8 with block 64), or rhs_per_thread 0 with block 128 -- the stencil of every
- * (site, rhs) pair split over two warps. */
-int wd_set_tile(wd_ctx* ctx, int L, int rhs_per_thread, int block, int min_blocks);
+/* Tile of the low-precision Jacobi sweep chosen by the autotuner for this L and storage
+ * (precision 1: FP32 blocks, 3: BF16 blocks): RHS per thread, threads per CTA, the minimum
+ * resident CTAs per SM the kernel was compiled for (0: none; 8: at most 128 registers a thread),
+ * and whether each direction's neighbour data is staged in shared memory (cp.async, two stages)
+ * while the previous direction is computed.  The autotuner times every candidate tile once, at
+ * the first preconditioner call with that L and storage, and keeps the fastest in the context.
+ * WD_EINVAL until then.  Any output pointer may be NULL. */
+int wd_tuned_tile(const wd_ctx* ctx, int L, int precision, int* rhs_per_thread, int* block,
+                  int* min_blocks, int* staged);
+/* Sets that tile by hand instead: rhs_per_thread 1 or 2 dividing L with block 64, 128 or 256,
+ * min_blocks 0 (or 8 with block 64) and staged 0; rhs_per_thread 0 with block 128 (the stencil of
+ * every (site, rhs) pair split over two warps); or staged 1 with rhs_per_thread 2, block 64 and
+ * min_blocks 0. */
+int wd_set_tile(wd_ctx* ctx, int L, int precision, int rhs_per_thread, int block, int min_blocks,
+                int staged);
+
+/* Link format of the low-precision sweeps: 12 (rows 0 and 1 of each FP32 link are read and row 2
+ * is rebuilt as conj(row0 x row1), which holds for SU(3)) or 18 (all three rows read).  wd_create
+ * picks 12 when every link's third row matches conj(row0 x row1) to 1e-6 per entry, else 18.
+ * wd_set_link_reals(ctx, 18) forces the full format; asking for 12 with links that failed the
+ * check is WD_EINVAL.  The FP64 path and the learned network always read 18 reals. */
+int wd_link_reals(const wd_ctx* ctx, int* reals);
+int wd_set_link_reals(wd_ctx* ctx, int reals);
 
 /* Lattice size and parameters of a context (for bindings): dims[4], V, kappa, c_SW. */
 int wd_query(const wd_ctx* ctx, int dims[4], long long* volume, double* kappa, double* csw);

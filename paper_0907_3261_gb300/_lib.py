@@ -92,7 +92,7 @@ def lib():
     L.wd_net_num_weights.restype = C.c_longlong
     L.wd_net_set_weights.argtypes = [vp, vp]
     L.wd_net_get_weights.argtypes = [vp, vp]
-    L.wd_net_apply.argtypes = [vp, vp, vp, vp, i, vp]
+    L.wd_net_apply.argtypes = [vp, vp, vp, vp, i, i, vp]
     L.wd_net_loss_grad.argtypes = [vp, vp, vp, vp, i, C.POINTER(d), vp, vp]
     L.wd_net_adam_step.argtypes = [vp, d, vp]
     for name in ("wd_net_create", "wd_net_set_weights", "wd_net_get_weights", "wd_net_apply",
@@ -101,10 +101,15 @@ def lib():
     L.wd_profile_enable.argtypes = [vp, i]
     L.wd_profile_reset.argtypes = [vp]
     L.wd_profile_read.argtypes = [vp, i, C.POINTER(C.c_longlong), C.POINTER(d)]
-    L.wd_tuned_tile.argtypes = [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.wd_tuned_tile.argtypes = [vp, i, i, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.wd_tuned_tile.restype = C.c_int
-    L.wd_set_tile.argtypes = [vp, i, i, i, i]
+    L.wd_set_tile.argtypes = [vp, i, i, i, i, i, i]
     L.wd_set_tile.restype = C.c_int
+    L.wd_link_reals.argtypes = [vp, C.POINTER(C.c_int)]
+    L.wd_link_reals.restype = C.c_int
+    L.wd_set_link_reals.argtypes = [vp, i]
+    L.wd_set_link_reals.restype = C.c_int
     L.wd_profile_name.argtypes = [i]
     L.wd_profile_name.restype = C.c_char_p
     for name in ("wd_create", "wd_apply", "jacobi_precond", "jacobi_precond_noalloc",
@@ -214,7 +219,8 @@ def wd_apply(ctx: Context, X, Y=None, stream=None):
 
 
 def jacobi_precond(ctx: Context, R, j: int, G=None, precision: int = 0, stream=None):
-    """G = M R, j Jacobi sweeps from G = 0 (precision 0 = FP64, 1 = FP32 sweeps)."""
+    """G = M R, j Jacobi sweeps from G = 0 (precision 0 = FP64, 1 = FP32 sweeps, 3 = FP32
+    arithmetic on BF16-stored blocks)."""
     pr, L, kr = _ptr_and_L(R, "R")
     if G is None:
         G = _empty_like(R)
@@ -277,7 +283,7 @@ def bbicggr_solve(ctx: Context, B, X=None, j: int = 12, tol: float = 1e-12, maxi
     return X, out
 
 
-WD_K_COUNT = 14
+WD_K_COUNT = 15
 
 
 def wd_profile_enable(ctx: Context, timing_on: bool = True) -> None:
@@ -300,17 +306,33 @@ def wd_profile_read(ctx: Context) -> dict:
     return out
 
 
-def wd_tuned_tile(ctx: Context, L: int):
-    """(RHS per thread, threads per CTA, min CTAs per SM) of the FP32 sweep for L, or None."""
-    r, b, m = C.c_int(), C.c_int(), C.c_int()
-    if lib().wd_tuned_tile(ctx.handle, int(L), C.byref(r), C.byref(b), C.byref(m)) != WD_OK:
+def wd_tuned_tile(ctx: Context, L: int, precision: int = 1):
+    """(RHS per thread, threads per CTA, min CTAs per SM, staged) of the low-precision sweep for
+    L (precision 1: FP32 blocks, 3: BF16 blocks), or None before the autotuner ran."""
+    r, b, m, st = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    if lib().wd_tuned_tile(ctx.handle, int(L), int(precision), C.byref(r), C.byref(b),
+                           C.byref(m), C.byref(st)) != WD_OK:
         return None
-    return int(r.value), int(b.value), int(m.value)
+    return int(r.value), int(b.value), int(m.value), int(st.value)
 
 
-def wd_set_tile(ctx: Context, L: int, rhs_per_thread: int, block: int, min_blocks: int = 0) -> None:
-    """Fix the FP32 sweep's tile for this L instead of autotuning it."""
-    _check(lib().wd_set_tile(ctx.handle, int(L), int(rhs_per_thread), int(block), int(min_blocks)))
+def wd_set_tile(ctx: Context, L: int, rhs_per_thread: int, block: int, min_blocks: int = 0,
+                staged: int = 0, precision: int = 1) -> None:
+    """Fix the low-precision sweep's tile for this L and storage instead of autotuning it."""
+    _check(lib().wd_set_tile(ctx.handle, int(L), int(precision), int(rhs_per_thread), int(block),
+                             int(min_blocks), int(staged)))
+
+
+def wd_link_reals(ctx: Context) -> int:
+    """12 when the low-precision sweeps rebuild row 2 of each link, 18 when they read it."""
+    r = C.c_int()
+    _check(lib().wd_link_reals(ctx.handle, C.byref(r)))
+    return int(r.value)
+
+
+def wd_set_link_reals(ctx: Context, reals: int) -> None:
+    """Choose the link format of the low-precision sweeps (12 needs special unitary links)."""
+    _check(lib().wd_set_link_reals(ctx.handle, int(reals)))
 
 
 
@@ -380,13 +402,13 @@ def wd_net_set_weights(net: Net, weights) -> None:
     _check(lib().wd_net_set_weights(net.handle, C.c_void_p(flat.ctypes.data)))
 
 
-def wd_net_apply(ctx: Context, net: Net, R, G=None, stream=None):
-    """G = N(R) for device (torch) blocks."""
+def wd_net_apply(ctx: Context, net: Net, R, G=None, bf16: bool = False, stream=None):
+    """G = N(R) for device (torch) blocks; bf16 stores the activations in BF16."""
     pr, L, kr = _ptr_and_L(R, "R")
     if G is None:
         G = _empty_like(R)
     pg, _, kg = _ptr_and_L(G, "G")
-    _check(lib().wd_net_apply(ctx.handle, net.handle, pr, pg, L, _stream(stream)))
+    _check(lib().wd_net_apply(ctx.handle, net.handle, pr, pg, L, int(bool(bf16)), _stream(stream)))
     return G
 
 

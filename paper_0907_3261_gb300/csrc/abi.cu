@@ -115,14 +115,18 @@ struct wd_ctx {
   double* bnorm2_dev = nullptr;
   // staging for host pointers in wd_apply / jacobi_precond
   DevBuf stage_in, stage_out;
-  // FP32 preconditioner blocks: U in FP32 and two sweep buffers
+  // low-precision preconditioner blocks: U and two sweep buffers (sized for FP32 elements)
   DevBuf blk32[3];
-  // autotuned tile of the FP32 sweep per L: RHS per thread and threads per CTA (0 = not tuned)
-  int tile_r[WD_LMAX + 1] = {};
-  int tile_block[WD_LMAX + 1] = {};
-  int tile_minb[WD_LMAX + 1] = {};
-  bool tile_set[WD_LMAX + 1] = {};
+  // autotuned tile of the low-precision sweep per storage (LP_F32, LP_BF16) and L: RHS per
+  // thread, threads per CTA, min CTAs per SM, shared-memory staging
+  int tile_r[2][WD_LMAX + 1] = {};
+  int tile_block[2][WD_LMAX + 1] = {};
+  int tile_minb[2][WD_LMAX + 1] = {};
+  int tile_staged[2][WD_LMAX + 1] = {};
+  bool tile_set[2][WD_LMAX + 1] = {};
+  bool links_su3 = false;         // the links are special unitary to LINK12_TOL
   wd_net* active_net = nullptr;   // learned preconditioner of the running solve (mode 2)
+  bool net_bf16 = false;          // ... with its activations stored in BF16 (precision 3)
   // device-controlled (graph) solves
   void* gctl = nullptr;           // GraphCtl
   double* ghist = nullptr;        // residual history, ghist_len entries
@@ -131,6 +135,20 @@ struct wd_ctx {
 };
 
 namespace {
+
+// Preconditioner modes of precondition(): FP64 sweeps, FP32-storage sweeps, the learned network,
+// BF16-storage sweeps, double-float sweeps.
+enum { PM_F64 = 0, PM_F32 = 1, PM_NET = 2, PM_BF16 = 3, PM_DF = 4 };
+constexpr int DF_BLOCK = 128;   // threads per CTA of the double-float sweep
+inline int lp_storage(int mode) { return mode == PM_BF16 ? LP_BF16 : LP_F32; }
+// Mode for the public options: precision 1 and 2 sweep in FP32, 3 in BF16, 4 in double-float; a
+// network wins.
+inline int precond_mode(const bbicggr_opts& o) {
+  if (o.net) return PM_NET;
+  if (o.precision == 3) return PM_BF16;
+  if (o.precision == 4) return PM_DF;
+  return o.precision >= 1 ? PM_F32 : PM_F64;
+}
 
 enum { B_R, B_P, B_V, B_W, B_F, B_U, B_G, B_Y, B_RT, B_T, B_CORE,
        B_B = B_CORE, B_XS, B_X0, B_COUNT };
@@ -218,16 +236,18 @@ int ensure_workspace(wd_ctx* c, int L) {
   return WD_OK;
 }
 
-// Picks the FP32 sweep's tile (RHS per thread, threads per CTA) for this lattice and L by timing
-// every candidate on the context's FP32 blocks (zeroed first); the winner is kept in the context.
-int autotune_f32(wd_ctx* c, int L, cudaStream_t s) {
-  static const int cand[][3] = {{1, 64, 0}, {1, 128, 0}, {1, 256, 0}, {2, 64, 0}, {2, 128, 0},
-                                {2, 256, 0}, {0, 128, 0}, {2, 64, 8}};
-  const size_t bytes = (size_t)c->op.g.V * 12 * L * 8;
-  float* u32 = static_cast<float*>(c->blk32[0].p);
-  float* a = static_cast<float*>(c->blk32[1].p);
-  float* b = static_cast<float*>(c->blk32[2].p);
-  CU(cudaMemsetAsync(u32, 0, bytes, s));
+// Picks the low-precision sweep's tile (RHS per thread, threads per CTA, min CTAs per SM, staging) for this
+// lattice, storage and L by timing every candidate on the context's blocks (zeroed first); the
+// winner is kept in the context.
+int autotune_lp(wd_ctx* c, int storage, int L, cudaStream_t s) {
+  static const int cand[][4] = {{1, 64, 0, 0},  {1, 128, 0, 0}, {1, 256, 0, 0}, {2, 64, 0, 0},
+                                {2, 128, 0, 0}, {2, 256, 0, 0}, {0, 128, 0, 0}, {2, 64, 8, 0},
+                                {2, 64, 0, 1}};
+  const size_t bytes = (size_t)c->op.g.V * 12 * L * lp_elem_bytes(storage);
+  void* u_lp = c->blk32[0].p;
+  void* a = c->blk32[1].p;
+  void* b = c->blk32[2].p;
+  CU(cudaMemsetAsync(u_lp, 0, bytes, s));
   CU(cudaMemsetAsync(a, 0, bytes, s));
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
@@ -237,10 +257,13 @@ int autotune_f32(wd_ctx* c, int L, cudaStream_t s) {
   cudaError_t err = cudaSuccess;
   for (int i = 0; i < (int)(sizeof(cand) / sizeof(cand[0])) && err == cudaSuccess; ++i) {
     if (cand[i][0] > 0 && L % cand[i][0] != 0) continue;
-    err = launch_jacobi_f32_tiled(c->op, a, u32, b, nullptr, L, cand[i][0], cand[i][1], cand[i][2], s);
+    if (cand[i][3] && L % 2 != 0) continue;
+    err = launch_jacobi_lp_tiled(c->op, storage, a, u_lp, b, nullptr, L, cand[i][0], cand[i][1],
+                                 cand[i][2], cand[i][3], s);
     if (err == cudaSuccess) err = cudaEventRecord(e0, s);
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
-      err = launch_jacobi_f32_tiled(c->op, a, u32, b, nullptr, L, cand[i][0], cand[i][1], cand[i][2], s);
+      err = launch_jacobi_lp_tiled(c->op, storage, a, u_lp, b, nullptr, L, cand[i][0], cand[i][1],
+                                   cand[i][2], cand[i][3], s);
     if (err == cudaSuccess) err = cudaEventRecord(e1, s);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -250,17 +273,25 @@ int autotune_f32(wd_ctx* c, int L, cudaStream_t s) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CU(err);
-  c->tile_r[L] = cand[best_i][0];
-  c->tile_block[L] = cand[best_i][1];
-  c->tile_minb[L] = cand[best_i][2];
-  c->tile_set[L] = true;
+  c->tile_r[storage][L] = cand[best_i][0];
+  c->tile_block[storage][L] = cand[best_i][1];
+  c->tile_minb[storage][L] = cand[best_i][2];
+  c->tile_staged[storage][L] = cand[best_i][3];
+  c->tile_set[storage][L] = true;
   return WD_OK;
 }
 
-int ensure_workspace32(wd_ctx* c, int L, cudaStream_t s) {
-  const size_t bytes = (size_t)c->op.g.V * 12 * L * 8;
+// Double-float blocks take 16 bytes per complex number, like FP64 blocks.
+int ensure_workspace_df(wd_ctx* c, int L) {
+  const size_t bytes = (size_t)c->op.g.V * 12 * L * 16;
   for (auto& b : c->blk32) CHECK(b.ensure(bytes));
-  if (!c->tile_set[L]) CHECK(autotune_f32(c, L, s));
+  return WD_OK;
+}
+
+int ensure_workspace_lp(wd_ctx* c, int storage, int L, cudaStream_t s) {
+  const size_t bytes = (size_t)c->op.g.V * 12 * L * lp_elem_bytes(LP_F32);
+  for (auto& b : c->blk32) CHECK(b.ensure(bytes));
+  if (!c->tile_set[storage][L]) CHECK(autotune_lp(c, storage, L, s));
   return WD_OK;
 }
 
@@ -280,40 +311,66 @@ int stage_input(const void* p, size_t bytes, DevBuf& stage, const double** out, 
 }
 
 // G = M R with j Jacobi sweeps; `a` and `b` are two FP64 scratch blocks, the result pointer is
-// returned in *res (one of a, b).  j = 0 copies R.  precision 1 runs the sweeps in FP32 (FP32
-// links, FP32 A_D^{-1}, FP32 accumulation) and writes the last one to `a` in FP64.
+// returned in *res (one of a, b).  j = 0 copies R.  Modes PM_F32 and PM_BF16 run the sweeps in
+// FP32 arithmetic (FP32 links and A_D^{-1}) on blocks stored in FP32 or BF16 and write the last
+// sweep to `a` in FP64.
 int precondition(wd_ctx* c, const double* R, double* a, double* b, double** res, int L, int j,
-                 int precision, long long* hop_count, cudaStream_t s) {
+                 int mode, long long* hop_count, cudaStream_t s) {
   const Op& op = c->op;
-  if (j == 0 && precision != 2) {
+  if (j == 0 && mode != PM_NET) {
     LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(a, R, block_bytes(c, L), cudaMemcpyDeviceToDevice, s));
     *res = a;
     return WD_OK;
   }
-  if (precision == 2) {   // learned network
+  if (mode == PM_NET) {   // learned network
     *res = a;
     Timed timed_(c, WD_K_NET, 0, s);
-    CHECK(wd_net_precondition(c, c->active_net, R, a, L, s));
+    CHECK(wd_net_precondition(c, c->active_net, R, a, L, c->net_bf16, s));
     return WD_OK;
   }
-  if (precision == 1) {
+  if (mode == PM_DF) {
     *res = a;
     if (j == 1) {
-      LAUNCH(WD_K_SITE_INV, 1, launch_site_inverse_mixed(op, R, nullptr, nullptr, a, L, s));
+      LAUNCH(WD_K_SITE_INV, 1, launch_site_inverse_df(op, R, nullptr, nullptr, a, L, s));
       return WD_OK;
     }
-    CHECK(ensure_workspace32(c, L, s));
-    float* u32 = static_cast<float*>(c->blk32[0].p);
-    float* cur = static_cast<float*>(c->blk32[1].p);
-    float* nxt = static_cast<float*>(c->blk32[2].p);
-    LAUNCH(WD_K_SITE_INV, 1, launch_site_inverse_mixed(op, R, u32, cur, nullptr, L, s));
+    CHECK(ensure_workspace_df(c, L));
+    void* u_df = c->blk32[0].p;
+    void* cur = c->blk32[1].p;
+    void* nxt = c->blk32[2].p;
+    LAUNCH(WD_K_SITE_INV, 1, launch_site_inverse_df(op, R, u_df, cur, nullptr, L, s));
     for (int i = 1; i < j; ++i) {
       const bool last = i == j - 1;
-      LAUNCH(WD_K_JACOBI, 1,
-             launch_jacobi_f32_tiled(op, cur, u32, last ? nullptr : nxt, last ? a : nullptr, L,
-                                     c->tile_r[L], c->tile_block[L], c->tile_minb[L], s));
+      LAUNCH(WD_K_JACOBI_LP, 1,
+             launch_jacobi_df(op, cur, u_df, last ? nullptr : nxt, last ? a : nullptr, L,
+                              DF_BLOCK, s));
       if (hop_count) ++*hop_count;
-      float* t = cur;
+      void* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    return WD_OK;
+  }
+  if (mode == PM_F32 || mode == PM_BF16) {
+    const int st = lp_storage(mode);
+    *res = a;
+    if (j == 1) {
+      LAUNCH(WD_K_SITE_INV, 1, launch_site_inverse_lp(op, st, R, nullptr, nullptr, a, L, s));
+      return WD_OK;
+    }
+    CHECK(ensure_workspace_lp(c, st, L, s));
+    void* u_lp = c->blk32[0].p;
+    void* cur = c->blk32[1].p;
+    void* nxt = c->blk32[2].p;
+    LAUNCH(WD_K_SITE_INV, 1, launch_site_inverse_lp(op, st, R, u_lp, cur, nullptr, L, s));
+    for (int i = 1; i < j; ++i) {
+      const bool last = i == j - 1;
+      LAUNCH(WD_K_JACOBI_LP, 1,
+             launch_jacobi_lp_tiled(op, st, cur, u_lp, last ? nullptr : nxt, last ? a : nullptr,
+                                    L, c->tile_r[st][L], c->tile_block[st][L],
+                                    c->tile_minb[st][L], c->tile_staged[st][L], s));
+      if (hop_count) ++*hop_count;
+      void* t = cur;
       cur = nxt;
       nxt = t;
     }
@@ -491,10 +548,6 @@ void wd_destroy(wd_ctx* c) {
   cudaFree(c->op.clov_inv32);
   for (auto& b : c->blk) b.release();
   for (auto& b : c->blk32) b.release();
-  for (int l = 0; l <= WD_LMAX; ++l) {
-    c->tile_r[l] = c->tile_block[l] = c->tile_minb[l] = 0;
-    c->tile_set[l] = false;
-  }
   c->part.release();
   c->stage_in.release();
   c->stage_out.release();
@@ -517,17 +570,19 @@ static int create_impl(wd_ctx* c, const void* links, const int dims[4], cudaStre
   CU(cudaMalloc(&op.links32, V * 4 * 18 * sizeof(float)));
   CU(cudaMalloc(&op.clov_inv32, V * 2 * CLOV_REALS * sizeof(float)));
   CU(cudaMemcpyAsync(op.links, links, lbytes, cudaMemcpyDefault, s));
-  int* flag;
-  CU(cudaMalloc(&flag, sizeof(int)));
-  CU(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  int* flag;   // [0]: a singular A_D block; [1]: a link that is not special unitary
+  CU(cudaMalloc(&flag, 2 * sizeof(int)));
+  CU(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
   CU(launch_clover_build(op, flag, s));
-  CU(launch_fp32_operator_copies(op, s));
-  int h = 0;
-  cudaError_t e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  CU(launch_lp_operator_copies(op, flag + 1, s));
+  int h[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(h, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(flag);
   CU(e);
-  if (h) {
+  c->links_su3 = h[1] == 0;
+  op.link12 = c->links_su3 ? 1 : 0;
+  if (h[0]) {
     set_err("a 6x6 clover block A_D is singular for kappa=%g c_SW=%g", op.kappa, op.csw);
     return WD_BREAKDOWN;
   }
@@ -589,33 +644,70 @@ int wd_profile_read(const wd_ctx* c, int cls, long long* launches, double* ms) {
 const char* wd_profile_name(int cls) {
   static const char* names[WD_K_COUNT] = {
       "dslash_apply", "dslash_resid", "dslash_jacobi", "site_inverse", "update_u", "update_xr",
-      "update_pv", "gram", "trace", "solve_ll", "colnorm", "copy", "convert", "net"};
+      "update_pv", "gram", "trace", "solve_ll", "colnorm", "copy", "convert", "net",
+      "dslash_jacobi_lp"};
   return (cls >= 0 && cls < WD_K_COUNT) ? names[cls] : "unknown";
 }
 
-int wd_set_tile(wd_ctx* c, int L, int rhs_per_thread, int block, int min_blocks) {
+static int tile_storage(int precision, int* storage) {
+  if (precision == 1) { *storage = LP_F32; return WD_OK; }
+  if (precision == 3) { *storage = LP_BF16; return WD_OK; }
+  set_err("precision %d has no sweep tile (1 = FP32, 3 = BF16 storage)", precision);
+  return WD_EINVAL;
+}
+
+int wd_set_tile(wd_ctx* c, int L, int precision, int rhs_per_thread, int block, int min_blocks,
+                int staged) {
   if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
   CHECK(check_L(L));
+  int st;
+  CHECK(tile_storage(precision, &st));
   const bool split = rhs_per_thread == 0 && block == 128 && min_blocks == 0;
   const bool capped = min_blocks == 8 && block == 64 && rhs_per_thread != 0;
-  if (!split && ((rhs_per_thread != 1 && rhs_per_thread != 2) || L % rhs_per_thread != 0 ||
-                 (block != 64 && block != 128 && block != 256) || (min_blocks != 0 && !capped))) {
-    set_err("tile (%d RHS/thread, %d threads, min %d blocks) not available for L = %d",
-            rhs_per_thread, block, min_blocks, L);
+  const bool pipe = staged == 1 && rhs_per_thread == 2 && block == 64 && min_blocks == 0 && L % 2 == 0;
+  if ((staged != 0 && !pipe) ||
+      (!staged && !split && ((rhs_per_thread != 1 && rhs_per_thread != 2) || L % rhs_per_thread != 0 ||
+                             (block != 64 && block != 128 && block != 256) ||
+                             (min_blocks != 0 && !capped)))) {
+    set_err("tile (%d RHS/thread, %d threads, min %d blocks, staged %d) not available for L = %d",
+            rhs_per_thread, block, min_blocks, staged, L);
     return WD_EINVAL;
   }
-  c->tile_r[L] = rhs_per_thread;
-  c->tile_block[L] = block;
-  c->tile_minb[L] = min_blocks;
-  c->tile_set[L] = true;
+  c->tile_r[st][L] = rhs_per_thread;
+  c->tile_block[st][L] = block;
+  c->tile_minb[st][L] = min_blocks;
+  c->tile_staged[st][L] = staged;
+  c->tile_set[st][L] = true;
   return WD_OK;
 }
 
-int wd_tuned_tile(const wd_ctx* c, int L, int* rhs_per_thread, int* block, int* min_blocks) {
-  if (!c || L < 1 || L > WD_LMAX || !c->tile_set[L]) { set_err("no tuned tile for this L"); return WD_EINVAL; }
-  if (rhs_per_thread) *rhs_per_thread = c->tile_r[L];
-  if (block) *block = c->tile_block[L];
-  if (min_blocks) *min_blocks = c->tile_minb[L];
+int wd_tuned_tile(const wd_ctx* c, int L, int precision, int* rhs_per_thread, int* block,
+                  int* min_blocks, int* staged) {
+  int st;
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  CHECK(tile_storage(precision, &st));
+  if (L < 1 || L > WD_LMAX || !c->tile_set[st][L]) { set_err("no tuned tile for this L"); return WD_EINVAL; }
+  if (rhs_per_thread) *rhs_per_thread = c->tile_r[st][L];
+  if (block) *block = c->tile_block[st][L];
+  if (min_blocks) *min_blocks = c->tile_minb[st][L];
+  if (staged) *staged = c->tile_staged[st][L];
+  return WD_OK;
+}
+
+int wd_link_reals(const wd_ctx* c, int* reals) {
+  if (!c || !reals) { set_err("ctx or reals is NULL"); return WD_EINVAL; }
+  *reals = c->op.link12 ? 12 : 18;
+  return WD_OK;
+}
+
+int wd_set_link_reals(wd_ctx* c, int reals) {
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  if (reals != 12 && reals != 18) { set_err("link format %d not in {12, 18}", reals); return WD_EINVAL; }
+  if (reals == 12 && !c->links_su3) {
+    set_err("the links are not special unitary to %g: their third rows cannot be rebuilt", LINK12_TOL);
+    return WD_EINVAL;
+  }
+  c->op.link12 = reals == 12 ? 1 : 0;
   return WD_OK;
 }
 
@@ -654,7 +746,10 @@ int jacobi_precond(wd_ctx* c, const void* R, void* G, int L, int j, int precisio
   CHECK(check_ptr(R, "R"));
   CHECK(check_ptr(G, "G"));
   if (j < 0) { set_err("j = %d < 0", j); return WD_EINVAL; }
-  if (precision != 0 && precision != 1) { set_err("precision %d not in {0, 1}", precision); return WD_EINVAL; }
+  if (precision != PM_F64 && precision != PM_F32 && precision != PM_BF16 && precision != PM_DF) {
+    set_err("precision %d not in {0, 1, 3, 4}", precision);
+    return WD_EINVAL;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = block_bytes(c, L);
   const double* rd;
@@ -671,7 +766,7 @@ int jacobi_precond(wd_ctx* c, const void* R, void* G, int L, int j, int precisio
   // first buffer when j is odd.
   double* first = (j % 2 == 1) ? gd : tmp;
   double* second = (j % 2 == 1) ? tmp : gd;
-  if (precision == 1) { first = gd; second = tmp; }   // the FP32 sweeps always finish in `first`
+  if (precision != PM_F64) { first = gd; second = tmp; }   // low-precision sweeps finish in `first`
   CHECK(precondition(c, rd, first, second, &res, L, j, precision, nullptr, s));
   if (res != gd) LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(gd, res, bytes, cudaMemcpyDeviceToDevice, s));
   if (!g_dev) CU(cudaMemcpyAsync(G, gd, bytes, cudaMemcpyDeviceToHost, s));
@@ -696,7 +791,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     set_err("invalid options");
     return WD_EINVAL;
   }
-  if (o.precision < 0 || o.precision > 2) { set_err("precision %d not in {0, 1, 2}", o.precision); return WD_EINVAL; }
+  if (o.precision < 0 || o.precision > 4) { set_err("precision %d not in {0, ..., 4}", o.precision); return WD_EINVAL; }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CHECK(ensure_workspace(c, L));
   const size_t bytes = block_bytes(c, L);
@@ -726,9 +821,10 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     }
 
   int status = WD_OK, iters = 0, restarts = 0, hist_n = 0, fallbacks = 0;
-  int prec = o.net ? 2 : (o.precision >= 1 ? 1 : 0);
+  int prec = precond_mode(o);
   bool df = o.precision == 2;
   c->active_net = o.net;
+  c->net_bf16 = o.net && o.precision == 3;
   const bool may_fall_back = prec != 0 && o.stall_window > 0;
   if (may_fall_back) CHECK(c->blk[B_X0].ensure(bytes));
   if (may_fall_back)   // keep X_0 for a restart with the FP64 preconditioner
@@ -1018,7 +1114,7 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     }
     const bbicggr_opts& o = jb.opts;
     if (o.maxit < 0 || !(o.div_thresh > 0.0) || o.stall_window < 0 ||
-        o.precision < 0 || o.precision > 2) {
+        o.precision < 0 || o.precision > 4) {
       set_err("job %d: invalid options", i);
       return WD_EINVAL;
     }
@@ -1028,9 +1124,11 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     bbicggr_job& jb = jobs[i];
     wd_ctx* c = jb.ctx;
     CHECK(ensure_workspace(c, jb.L));
-    const int mode = jb.opts.net ? 2 : (jb.opts.precision >= 1 ? 1 : 0);
-    if (mode == 1 && jb.j >= 2) CHECK(ensure_workspace32(c, jb.L, s));
-    if (mode == 2) CHECK(wd_net_prepare(c, jb.opts.net, jb.L));
+    const int mode = precond_mode(jb.opts);
+    if ((mode == PM_F32 || mode == PM_BF16) && jb.j >= 2)
+      CHECK(ensure_workspace_lp(c, lp_storage(mode), jb.L, s));
+    if (mode == PM_DF && jb.j >= 2) CHECK(ensure_workspace_df(c, jb.L));
+    if (mode == PM_NET) CHECK(wd_net_prepare(c, jb.opts.net, jb.L));
     if (!c->gctl) CU(cudaMalloc(&c->gctl, sizeof(GraphCtl)));
     const int hl = jb.opts.history ? jb.opts.history_len : 0;
     if (hl > c->ghist_len) {
@@ -1060,8 +1158,9 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     const bool timing = c->prof.timing;
     c->prof.timing = false;                 // no event nodes in the graph
     c->active_net = jb.opts.net;
+    c->net_bf16 = jb.opts.net && jb.opts.precision == 3;
     JobPtrs jp{static_cast<const double*>(jb.B), static_cast<double*>(jb.X), jb.L, jb.j,
-               jb.opts.net ? 2 : (jb.opts.precision >= 1 ? 1 : 0), jb.opts.precision == 2, jb.tol};
+               precond_mode(jb.opts), jb.opts.precision == 2, jb.tol};
     rc = build_job(c, jp, G);
     c->prof.timing = timing;
   }

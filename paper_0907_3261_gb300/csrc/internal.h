@@ -19,7 +19,13 @@ struct Op {
   double* clov_inv;  // [V][2][36]  A_D^{-1} blocks
   float* links32;     // [4 mu][9 entries][V] complex, FP32 (component-major)
   float* clov_inv32;  // [2 chirality][36][V], FP32 (component-major)
+  // 1: the low-precision sweeps read rows 0 and 1 of each FP32 link and rebuild row 2 (the links
+  // are special unitary to LINK12_TOL); 0: they read all three rows.
+  int link12;
 };
+
+// Largest entry error |row2 - conj(row0 x row1)| of a link that still counts as special unitary.
+constexpr double LINK12_TOL = 1e-6;
 
 // ---- dslash.cu (FP64)
 cudaError_t launch_apply_f64(const Op& op, const double* x, double* y, int L, cudaStream_t st);
@@ -30,19 +36,45 @@ cudaError_t launch_jacobi_f64(const Op& op, const double* g_in, const double* u,
 cudaError_t launch_site_inverse_f64(const Op& op, const double* u, double* g_out, int L,
                                     cudaStream_t st);
 
-// ---- dslash.cu: the FP32 preconditioner.  Its blocks (u32, g32) are component-major,
-// [spin*3+colour][site][rhs]; FP64 blocks are site-major.  Exactly one of g32 / g64 is non-null.
-cudaError_t launch_fp32_operator_copies(const Op& op, cudaStream_t st);
-cudaError_t launch_site_inverse_mixed(const Op& op, const double* u, float* u32, float* g32,
-                                      double* g64, int L, cudaStream_t st);
+// ---- sweep_lp.cu, sweep_f32.cu, sweep_bf16.cu: the low-precision preconditioner.  Its private
+// blocks (u_lp, g_lp) are component-major, [spin*3+colour][site][rhs], one complex number per
+// element: float2 (LP_F32) or two packed BF16 numbers (LP_BF16); FP64 blocks are site-major.
+// Exactly one of g_lp / g64 is non-null.
+enum { LP_F32 = 0, LP_BF16 = 1 };
+constexpr size_t lp_elem_bytes(int storage) { return storage == LP_BF16 ? 4 : 8; }
 
-// FP32 sweep with `rhs_per_thread` (1 or 2; divides L) RHS per thread and `block` threads (64,
+// FP32 component-major links and A_D^{-1}; sets *not_su3 (device) when some link is not special
+// unitary to LINK12_TOL.
+cudaError_t launch_lp_operator_copies(const Op& op, int* not_su3, cudaStream_t st);
+// First sweep from G = 0: G = A_D^{-1} U, with the low-precision copy of U stored in u_lp.
+cudaError_t launch_site_inverse_lp(const Op& op, int storage, const double* u, void* u_lp,
+                                   void* g_lp, double* g64, int L, cudaStream_t st);
+// One sweep with `rhs_per_thread` (1 or 2; divides L) RHS per thread and `block` threads (64,
 // 128, 256) per CTA -- with min_blocks 8 and block 64 compiled for at most 128 registers -- or,
-// rhs_per_thread 0, the stencil of each pair split over two warps (block 128); exactly one of
-// g32 / g64 is non-null.
-cudaError_t launch_jacobi_f32_tiled(const Op& op, const float* g_in, const float* u32, float* g32,
+// rhs_per_thread 0, the stencil of each pair split over two warps (block 128); staged 1 (with 2
+// RHS per thread and block 64) stages each direction's neighbour data in shared memory with
+// cp.async while the previous direction is computed.
+cudaError_t launch_jacobi_lp_tiled(const Op& op, int storage, const void* g_in, const void* u_lp,
+                                   void* g_lp, double* g64, int L, int rhs_per_thread, int block,
+                                   int min_blocks, int staged, cudaStream_t st);
+// The same per storage type.
+cudaError_t launch_site_inverse_f32(const Op& op, const double* u, void* u_lp, void* g_lp,
+                                    double* g64, int L, cudaStream_t st);
+cudaError_t launch_site_inverse_bf16(const Op& op, const double* u, void* u_lp, void* g_lp,
+                                     double* g64, int L, cudaStream_t st);
+cudaError_t launch_jacobi_f32_tiled(const Op& op, const void* g_in, const void* u_lp, void* g_lp,
                                     double* g64, int L, int rhs_per_thread, int block,
-                                    int min_blocks, cudaStream_t st);
+                                    int min_blocks, int staged, cudaStream_t st);
+cudaError_t launch_jacobi_bf16_tiled(const Op& op, const void* g_in, const void* u_lp, void* g_lp,
+                                     double* g64, int L, int rhs_per_thread, int block,
+                                     int min_blocks, int staged, cudaStream_t st);
+
+// ---- sweep_df.cu: the double-float preconditioner (FP32 operator, spinors as FP32 pairs).  Its
+// blocks are component-major with one float4 (re.hi, re.lo, im.hi, im.lo) per complex number.
+cudaError_t launch_site_inverse_df(const Op& op, const double* u, void* u_df, void* g_df,
+                                   double* g64, int L, cudaStream_t st);
+cudaError_t launch_jacobi_df(const Op& op, const void* g_in, const void* u_df, void* g_df,
+                             double* g64, int L, int block, cudaStream_t st);
 
 // ---- clover.cu
 // Builds clov and clov_inv from links; *singular_dev receives 1 if some 6x6 block is singular.
@@ -95,15 +127,19 @@ struct wd_ctx;
 const Op* wd_ctx_op(const wd_ctx* ctx);
 void wd_set_error(const char* fmt, ...);
 
-// ---- net.cu: the learned preconditioner (activations FP32, component-major per channel)
+// ---- net.cu: the learned preconditioner (activations component-major per channel)
 cudaError_t net_launch_layer(const Op& op, const float* in, float* out, const float2* W, int cin,
                              int cout, int L, cudaStream_t st);
 cudaError_t net_launch_wgrad(const Op& op, const float* in, const float* delta, int cin, int cout,
                              int L, double2* part, int nblocks, double2* grad, cudaStream_t st);
 cudaError_t net_launch_adjoint_weights(const float2* W, float2* Wa, int cin, int cout,
                                        cudaStream_t st);
-cudaError_t net_launch_to_cm(const double* x, float* y, int V, int L, cudaStream_t st);
-cudaError_t net_launch_from_cm(const float* y, double* x, int V, int L, cudaStream_t st);
+// FP64 site-major <-> component-major channel of FP32 (bf16 false) or BF16 elements.
+cudaError_t net_launch_to_cm(const double* x, void* y, int V, int L, bool bf16, cudaStream_t st);
+cudaError_t net_launch_from_cm(const void* y, double* x, int V, int L, bool bf16, cudaStream_t st);
+// One layer on BF16-stored activations (inference).
+cudaError_t net_launch_layer_bf16(const Op& op, const void* in, void* out, const float2* W,
+                                  int cin, int cout, int L, cudaStream_t st);
 cudaError_t net_launch_loss_delta(const float* y, const double* E, const double* wcol,
                                   float* delta, double* part, int nblocks, double* loss, int V,
                                   int L, cudaStream_t st);
@@ -111,6 +147,7 @@ cudaError_t net_launch_adam(float2* W, const double2* G, float2* m, float2* v, i
                             float b1, float b2, float eps, int t, cudaStream_t st);
 // ---- net_abi.cu
 struct wd_net;
-int wd_net_precondition(wd_ctx* ctx, wd_net* net, const double* R, double* G, int L,
+// G = N(R); bf16: activations stored in BF16.
+int wd_net_precondition(wd_ctx* ctx, wd_net* net, const double* R, double* G, int L, bool bf16,
                         cudaStream_t s);
 int wd_net_prepare(wd_ctx* ctx, wd_net* net, int L);

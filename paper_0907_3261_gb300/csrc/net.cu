@@ -5,8 +5,9 @@
 // covariant.  A layer maps C_in to C_out channels of spinor fields:
 //     out_{c'}(x) = sum_{d=0..8} sum_c W[d][c'][c] (T_d psi_c)(x),
 //     T_0 psi = psi,  T_{1+mu} psi(x) = U_mu(x) psi(x+mu),  T_{5+mu} psi(x) = U_mu(x-mu)^H psi(x-mu),
-// W[d][c'][c] a complex 4x4 spin matrix.  Activations are FP32, component-major per channel,
-// [channel][spin*3+colour][site][rhs]; weights are complex64, [9][C_out][C_in][4][4] per layer.
+// W[d][c'][c] a complex 4x4 spin matrix.  Activations are component-major per channel,
+// [channel][spin*3+colour][site][rhs], stored in FP32 (training and inference) or BF16 (inference
+// only), with FP32 arithmetic; weights are complex64, [9][C_out][C_in][4][4] per layer.
 // Training minimises (1/L) sum_i ||N(r_i) - e_i||^2 / ||e_i||^2 over pairs (r_i, e_i = A^{-1} r_i):
 // the backward pass runs each layer's adjoint (T_d^H = T_{opposite d}, W -> W^H, channels swapped)
 // with the same layer kernel, and the weight gradient d loss / d conj(W) is a deterministic
@@ -16,6 +17,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "elem.cuh"
 #include "internal.h"
 
 namespace {
@@ -49,24 +51,24 @@ WD_DEV void colour_mult(const float* __restrict__ U, size_t V, Cx<float> v[12]) 
 }
 
 // T_d psi at site s for one channel of a component-major block; x points at the channel.
-template <int D>
-WD_DEV void transport_at(const float* __restrict__ x, const float* __restrict__ links,
+template <int D, typename E>
+WD_DEV void transport_at(const E* __restrict__ x, const float* __restrict__ links,
                          const Geom& g, int s, const int c[4], int r, int L, Cx<float> v[12]) {
   const size_t V = (size_t)g.V;
   int sn = s;
   if constexpr (D >= 1 && D <= 4) sn = neighbour(g, s, c, D - 1, +1);
   if constexpr (D >= 5) sn = neighbour(g, s, c, D - 5, -1);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) v[k] = ldc(x + 2 * (((size_t)k * V + sn) * L + r));
+  for (int k = 0; k < 12; ++k) v[k] = lp::ld1(x + ((size_t)k * V + sn) * L + r);
   if constexpr (D >= 1 && D <= 4) colour_mult<+1>(links + 2 * ((size_t)(D - 1) * 9 * V + s), V, v);
   if constexpr (D >= 5) colour_mult<-1>(links + 2 * ((size_t)(D - 5) * 9 * V + sn), V, v);
 }
 
-template <int CIN, int COUT, int D>
-WD_DEV void layer_dir(const float* __restrict__ in, const float* __restrict__ links,
+template <int CIN, int COUT, int D, typename E>
+WD_DEV void layer_dir(const E* __restrict__ in, const float* __restrict__ links,
                       const float2* Ws, const Geom& g, int s, const int c[4], int r, int L,
                       Cx<float> acc[COUT][12]) {
-  const size_t chan = (size_t)12 * g.V * L * 2;   // floats per channel
+  const size_t chan = (size_t)12 * g.V * L;   // elements per channel
 #pragma unroll
   for (int ci = 0; ci < CIN; ++ci) {
     Cx<float> v[12];
@@ -87,9 +89,9 @@ WD_DEV void layer_dir(const float* __restrict__ in, const float* __restrict__ li
   }
 }
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, typename E>
 __global__ void __launch_bounds__(NET_THREADS)
-net_layer_kernel(const float* __restrict__ in, float* __restrict__ out,
+net_layer_kernel(const E* __restrict__ in, E* __restrict__ out,
                  const float* __restrict__ links, const float2* __restrict__ W, Geom g, int L) {
   __shared__ float2 Ws[9 * COUT * CIN * 16];
   for (int e = threadIdx.x; e < 9 * COUT * CIN * 16; e += blockDim.x) Ws[e] = W[e];
@@ -105,21 +107,21 @@ net_layer_kernel(const float* __restrict__ in, float* __restrict__ out,
   for (int co = 0; co < COUT; ++co)
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[co][k] = czero<float>();
-  layer_dir<CIN, COUT, 0>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 1>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 2>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 3>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 4>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 5>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 6>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 7>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 8>(in, links, Ws, g, s, c, r, L, acc);
+  layer_dir<CIN, COUT, 0, E>(in, links, Ws, g, s, c, r, L, acc);
+  layer_dir<CIN, COUT, 1, E>(in, links, Ws, g, s, c, r, L, acc);
+  layer_dir<CIN, COUT, 2, E>(in, links, Ws, g, s, c, r, L, acc);
+  layer_dir<CIN, COUT, 3, E>(in, links, Ws, g, s, c, r, L, acc);
+  layer_dir<CIN, COUT, 4, E>(in, links, Ws, g, s, c, r, L, acc);
+  layer_dir<CIN, COUT, 5, E>(in, links, Ws, g, s, c, r, L, acc);
+  layer_dir<CIN, COUT, 6, E>(in, links, Ws, g, s, c, r, L, acc);
+  layer_dir<CIN, COUT, 7, E>(in, links, Ws, g, s, c, r, L, acc);
+  layer_dir<CIN, COUT, 8, E>(in, links, Ws, g, s, c, r, L, acc);
   const size_t V = (size_t)g.V;
-  const size_t chan = (size_t)12 * V * L * 2;
+  const size_t chan = (size_t)12 * V * L;
 #pragma unroll
   for (int co = 0; co < COUT; ++co)
 #pragma unroll
-    for (int k = 0; k < 12; ++k) stc(out + co * chan + 2 * (((size_t)k * V + s) * L + r), acc[co][k]);
+    for (int k = 0; k < 12; ++k) lp::st1(out + co * chan + ((size_t)k * V + s) * L + r, acc[co][k]);
 }
 
 // W^adj[d'][c][c'] = W[d][c'][c]^H with d' the opposite direction of d (0 stays 0).
@@ -137,22 +139,24 @@ __global__ void adjoint_weights_kernel(const float2* __restrict__ W, float2* __r
   Wa[((da * cin + ci) * cout + co) * 16 + t * 4 + sp] = make_float2(w.x, -w.y);
 }
 
-// FP64 site-major block -> FP32 component-major channel, and back.
-__global__ void to_cm_kernel(const double* __restrict__ x, float* __restrict__ y, int V, int L) {
+// FP64 site-major block -> component-major channel (FP32 or BF16 elements), and back.
+template <typename E>
+__global__ void to_cm_kernel(const double* __restrict__ x, E* __restrict__ y, int V, int L) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= V * L) return;
   const int s = tid / L, r = tid - (tid / L) * L;
   for (int k = 0; k < 12; ++k) {
     const Cx<double> a = ldc(x + 2 * (((size_t)s * 12 + k) * L + r));
-    stc(y + 2 * (((size_t)k * V + s) * L + r), cmake<float>((float)a.re, (float)a.im));
+    lp::st1(y + ((size_t)k * V + s) * L + r, cmake<float>((float)a.re, (float)a.im));
   }
 }
-__global__ void from_cm_kernel(const float* __restrict__ y, double* __restrict__ x, int V, int L) {
+template <typename E>
+__global__ void from_cm_kernel(const E* __restrict__ y, double* __restrict__ x, int V, int L) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= V * L) return;
   const int s = tid / L, r = tid - (tid / L) * L;
   for (int k = 0; k < 12; ++k) {
-    const Cx<float> a = ldc(y + 2 * (((size_t)k * V + s) * L + r));
+    const Cx<float> a = lp::ld1(y + ((size_t)k * V + s) * L + r);
     stc(x + 2 * (((size_t)s * 12 + k) * L + r), cmake<double>(a.re, a.im));
   }
 }
@@ -194,7 +198,7 @@ WD_DEV void stage_transport(const float* __restrict__ in, const float* __restric
   int c[4];
   site_coords(g, s, c);
   Cx<float> v[12];
-  transport_at<D>(in, links, g, s, c, r, L, v);
+  transport_at<D>(reinterpret_cast<const float2*>(in), links, g, s, c, r, L, v);
 #pragma unroll
   for (int k = 0; k < 12; ++k) dst[k * stride] = make_float2(v[k].re, v[k].im);
 }
@@ -317,13 +321,22 @@ __global__ void adam_kernel(float2* __restrict__ W, const double2* __restrict__ 
   W[e] = w;
 }
 
-template <int CIN, int COUT>
-cudaError_t run_layer(const Op& op, const float* in, float* out, const float2* W, int L,
-                      cudaStream_t st) {
+template <int CIN, int COUT, typename E>
+cudaError_t run_layer(const Op& op, const E* in, E* out, const float2* W, int L, cudaStream_t st) {
   const long long n = (long long)op.g.V * L;
-  net_layer_kernel<CIN, COUT><<<(unsigned)((n + NET_THREADS - 1) / NET_THREADS), NET_THREADS, 0, st>>>(
+  net_layer_kernel<CIN, COUT, E><<<(unsigned)((n + NET_THREADS - 1) / NET_THREADS), NET_THREADS, 0, st>>>(
       in, out, op.links32, W, op.g, L);
   return cudaGetLastError();
+}
+
+template <typename E>
+cudaError_t layer_by_channels(const Op& op, const E* in, E* out, const float2* W, int cin,
+                              int cout, int L, cudaStream_t st) {
+#define WD_LAYER(a, b) if (cin == a && cout == b) return run_layer<a, b, E>(op, in, out, W, L, st);
+  WD_LAYER(1, 4) WD_LAYER(4, 4) WD_LAYER(4, 1) WD_LAYER(1, 2) WD_LAYER(2, 2) WD_LAYER(2, 1)
+  WD_LAYER(1, 1)
+#undef WD_LAYER
+  return cudaErrorInvalidValue;
 }
 
 template <int CIN, int COUT>
@@ -338,11 +351,14 @@ cudaError_t run_wgrad(const Op& op, const float* in, const float* delta, int L, 
 // ------------------------------------------------------------------ launchers
 cudaError_t net_launch_layer(const Op& op, const float* in, float* out, const float2* W, int cin,
                              int cout, int L, cudaStream_t st) {
-#define WD_LAYER(a, b) if (cin == a && cout == b) return run_layer<a, b>(op, in, out, W, L, st);
-  WD_LAYER(1, 4) WD_LAYER(4, 4) WD_LAYER(4, 1) WD_LAYER(1, 2) WD_LAYER(2, 2) WD_LAYER(2, 1)
-  WD_LAYER(1, 1)
-#undef WD_LAYER
-  return cudaErrorInvalidValue;
+  return layer_by_channels(op, reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out),
+                           W, cin, cout, L, st);
+}
+
+cudaError_t net_launch_layer_bf16(const Op& op, const void* in, void* out, const float2* W,
+                                  int cin, int cout, int L, cudaStream_t st) {
+  return layer_by_channels(op, static_cast<const lp::bf16x2*>(in), static_cast<lp::bf16x2*>(out),
+                           W, cin, cout, L, st);
 }
 
 cudaError_t net_launch_wgrad(const Op& op, const float* in, const float* delta, int cin, int cout,
@@ -364,15 +380,21 @@ cudaError_t net_launch_adjoint_weights(const float2* W, float2* Wa, int cin, int
   return cudaGetLastError();
 }
 
-cudaError_t net_launch_to_cm(const double* x, float* y, int V, int L, cudaStream_t st) {
-  const long long n = (long long)V * L;
-  to_cm_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(x, y, V, L);
+cudaError_t net_launch_to_cm(const double* x, void* y, int V, int L, bool bf16, cudaStream_t st) {
+  const unsigned grid = (unsigned)(((long long)V * L + 127) / 128);
+  if (bf16)
+    to_cm_kernel<<<grid, 128, 0, st>>>(x, static_cast<lp::bf16x2*>(y), V, L);
+  else
+    to_cm_kernel<<<grid, 128, 0, st>>>(x, static_cast<float2*>(y), V, L);
   return cudaGetLastError();
 }
 
-cudaError_t net_launch_from_cm(const float* y, double* x, int V, int L, cudaStream_t st) {
-  const long long n = (long long)V * L;
-  from_cm_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(y, x, V, L);
+cudaError_t net_launch_from_cm(const void* y, double* x, int V, int L, bool bf16, cudaStream_t st) {
+  const unsigned grid = (unsigned)(((long long)V * L + 127) / 128);
+  if (bf16)
+    from_cm_kernel<<<grid, 128, 0, st>>>(static_cast<const lp::bf16x2*>(y), x, V, L);
+  else
+    from_cm_kernel<<<grid, 128, 0, st>>>(static_cast<const float2*>(y), x, V, L);
   return cudaGetLastError();
 }
 

@@ -99,10 +99,17 @@ int net_workspace(wd_net* n, long long V, int L) {
   return WD_OK;
 }
 
-// act[layers] = N(act[0]) (activations of every layer kept).
-int net_forward(const Op& op, wd_net* n, int L, cudaStream_t s) {
-  for (int l = 0; l < n->layers; ++l)
-    NCU(net_launch_layer(op, n->act[l], n->act[l + 1], n->W + n->off[l], n->ch[l], n->ch[l + 1], L, s));
+// act[layers] = N(act[0]) (activations of every layer kept); bf16: the activations are stored
+// in BF16 (the buffers, sized for FP32, hold them in their first half).
+int net_forward(const Op& op, wd_net* n, int L, cudaStream_t s, bool bf16 = false) {
+  for (int l = 0; l < n->layers; ++l) {
+    if (bf16)
+      NCU(net_launch_layer_bf16(op, n->act[l], n->act[l + 1], n->W + n->off[l], n->ch[l],
+                                n->ch[l + 1], L, s));
+    else
+      NCU(net_launch_layer(op, n->act[l], n->act[l + 1], n->W + n->off[l], n->ch[l],
+                           n->ch[l + 1], L, s));
+  }
   return WD_OK;
 }
 
@@ -146,12 +153,13 @@ int wd_net_prepare(wd_ctx* ctx, wd_net* n, int L) {
 }
 
 // Internal: G = N(R) for device blocks R, G (site-major FP64), used by the solver.
-int wd_net_precondition(wd_ctx* ctx, wd_net* n, const double* R, double* G, int L, cudaStream_t s) {
+int wd_net_precondition(wd_ctx* ctx, wd_net* n, const double* R, double* G, int L, bool bf16,
+                        cudaStream_t s) {
   const Op& op = *wd_ctx_op(ctx);
   NCHECK(net_workspace(n, op.g.V, L));
-  NCU(net_launch_to_cm(R, n->act[0], op.g.V, L, s));
-  NCHECK(net_forward(op, n, L, s));
-  NCU(net_launch_from_cm(n->act[n->layers], G, op.g.V, L, s));
+  NCU(net_launch_to_cm(R, n->act[0], op.g.V, L, bf16, s));
+  NCHECK(net_forward(op, n, L, s, bf16));
+  NCU(net_launch_from_cm(n->act[n->layers], G, op.g.V, L, bf16, s));
   return WD_OK;
 }
 
@@ -220,12 +228,13 @@ int wd_net_get_weights(const wd_net* n, void* out) {
   return WD_OK;
 }
 
-int wd_net_apply(wd_ctx* ctx, wd_net* n, const void* R, void* G, int L, void* stream) {
+int wd_net_apply(wd_ctx* ctx, wd_net* n, const void* R, void* G, int L, int bf16, void* stream) {
   if (!ctx || !n || !R || !G) { wd_set_error("NULL argument"); return WD_EINVAL; }
+  if (bf16 != 0 && bf16 != 1) { wd_set_error("bf16 = %d not in {0, 1}", bf16); return WD_EINVAL; }
   if (L < 1 || L > WD_LMAX) { wd_set_error("L = %d outside [1, %d]", L, WD_LMAX); return WD_EINVAL; }
   if (!dev_ptr(R) || !dev_ptr(G)) { wd_set_error("wd_net_apply takes device buffers"); return WD_EINVAL; }
   return wd_net_precondition(ctx, n, static_cast<const double*>(R), static_cast<double*>(G), L,
-                             static_cast<cudaStream_t>(stream));
+                             bf16 != 0, static_cast<cudaStream_t>(stream));
 }
 
 int wd_net_loss_grad(wd_ctx* ctx, wd_net* n, const void* R, const void* E, int L, double* loss,
@@ -238,7 +247,7 @@ int wd_net_loss_grad(wd_ctx* ctx, wd_net* n, const void* R, const void* E, int L
   const long long V = op.g.V;
   NCHECK(net_workspace(n, V, L));
   // forward, keeping the activations
-  NCU(net_launch_to_cm(static_cast<const double*>(R), n->act[0], (int)V, L, s));
+  NCU(net_launch_to_cm(static_cast<const double*>(R), n->act[0], (int)V, L, false, s));
   NCHECK(net_forward(op, n, L, s));
   // column weights 1 / (L ||e_i||^2), loss and delta = d loss / d conj(y)
   double2* npart = reinterpret_cast<double2*>(n->norms);

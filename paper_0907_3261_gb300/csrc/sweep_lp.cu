@@ -1,0 +1,71 @@
+// The low-precision preconditioner's operator copies (FP32, component-major) and the dispatch of
+// its sweeps by storage type.
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+__global__ void links_to_cm_kernel(const double* __restrict__ links, float* __restrict__ out, int V) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  for (int mu = 0; mu < 4; ++mu)
+    for (int e = 0; e < 9; ++e) {
+      const double* p = links + 18 * ((size_t)s * 4 + mu) + 2 * e;
+      float* q = out + 2 * ((size_t)(mu * 9 + e) * V + s);
+      q[0] = (float)p[0];
+      q[1] = (float)p[1];
+    }
+}
+
+__global__ void clover_to_cm_kernel(const double* __restrict__ cl, float* __restrict__ out, int V) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  for (int ch = 0; ch < 2; ++ch)
+    for (int t = 0; t < CLOV_REALS; ++t)
+      out[(size_t)(ch * CLOV_REALS + t) * V + s] = (float)cl[((size_t)s * 2 + ch) * CLOV_REALS + t];
+}
+
+// Sets *not_su3 when some link's third row differs from conj(row0 x row1) by more than tol in
+// some entry (checked in FP64 on the caller's links).
+__global__ void su3_check_kernel(const double* __restrict__ links, int V, double tol,
+                                 int* __restrict__ not_su3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 4 * V) return;
+  const double* p = links + 18 * (size_t)i;
+  Cx<double> m[3][3];
+  for (int e = 0; e < 9; ++e) m[e / 3][e % 3] = cmake<double>(p[2 * e], p[2 * e + 1]);
+  const Cx<double> r[3] = {conj(cmul(m[0][1], m[1][2]) - cmul(m[0][2], m[1][1])),
+                           conj(cmul(m[0][2], m[1][0]) - cmul(m[0][0], m[1][2])),
+                           conj(cmul(m[0][0], m[1][1]) - cmul(m[0][1], m[1][0]))};
+  double err = 0.0;
+  for (int b = 0; b < 3; ++b) err = fmax(err, sqrt(cnorm2(r[b] - m[2][b])));
+  if (!(err <= tol)) *not_su3 = 1;   // NaN counts as a violation
+}
+
+}  // namespace
+
+cudaError_t launch_lp_operator_copies(const Op& op, int* not_su3, cudaStream_t st) {
+  const int threads = 128;
+  const unsigned grid = (unsigned)((op.g.V + threads - 1) / threads);
+  links_to_cm_kernel<<<grid, threads, 0, st>>>(op.links, op.links32, op.g.V);
+  clover_to_cm_kernel<<<grid, threads, 0, st>>>(op.clov_inv, op.clov_inv32, op.g.V);
+  const unsigned grid4 = (unsigned)((4LL * op.g.V + threads - 1) / threads);
+  su3_check_kernel<<<grid4, threads, 0, st>>>(op.links, op.g.V, LINK12_TOL, not_su3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_site_inverse_lp(const Op& op, int storage, const double* u, void* u_lp,
+                                   void* g_lp, double* g64, int L, cudaStream_t st) {
+  return storage == LP_BF16 ? launch_site_inverse_bf16(op, u, u_lp, g_lp, g64, L, st)
+                            : launch_site_inverse_f32(op, u, u_lp, g_lp, g64, L, st);
+}
+
+cudaError_t launch_jacobi_lp_tiled(const Op& op, int storage, const void* g_in, const void* u_lp,
+                                   void* g_lp, double* g64, int L, int rhs_per_thread, int block,
+                                   int min_blocks, int staged, cudaStream_t st) {
+  return storage == LP_BF16
+             ? launch_jacobi_bf16_tiled(op, g_in, u_lp, g_lp, g64, L, rhs_per_thread, block,
+                                        min_blocks, staged, st)
+             : launch_jacobi_f32_tiled(op, g_in, u_lp, g_lp, g64, L, rhs_per_thread, block,
+                                       min_blocks, staged, st);
+}

@@ -30,7 +30,8 @@ def host(t):
 
 
 CASES = [((4, 4, 4, 4), 4, 0.115, 4, 0), ((3, 4, 5, 6), 3, 0.12, 2, 0),
-         ((8, 8, 8, 16), 12, 0.13, 12, 1), ((4, 4, 4, 8), 1, 0.12, 3, 1), ((2, 2, 2, 2), 12, 0.115, 0, 0)]
+         ((8, 8, 8, 16), 12, 0.13, 12, 1), ((4, 4, 4, 8), 1, 0.12, 3, 1), ((2, 2, 2, 2), 12, 0.115, 0, 0),
+         ((4, 4, 4, 8), 6, 0.115, 4, 3), ((4, 4, 4, 4), 5, 0.12, 6, 4)]
 
 
 def test_batch_matches_host_controlled_solves(wd):

@@ -60,6 +60,39 @@ def test_net_forward_matches_oracle(wd, layers, hidden):
     assert all(np.array_equal(a, b) for a, b in zip(wd.wd_net_get_weights(net), W))
 
 
+@pytest.mark.parametrize("layers,hidden", [(4, 4), (3, 2)])
+def test_net_forward_bf16_activations(wd, layers, hidden):
+    """BF16-stored activations (inference): the input and every layer's output are rounded to
+    BF16 once (relative 2^-8 per component).  With the near-identity weights the training starts
+    from, each layer has norm ~1, so the layers + 1 roundings add up to at most (layers + 1) 2^-8."""
+    dims, U, _, R, _ = case(layers=layers, hidden=hidden)
+    W = [w.astype(np.complex64).astype(np.complex128)
+         for w in I.network_weights(layers, hidden, seed=2, noise=0.01)]
+    ctx = wd.wd_create(dev(U), dims, 0.13, 1.0)
+    net = wd.wd_net_create(layers, hidden, W)
+    Y = N.forward(U, O.Lattice(dims), W, R)[0]
+    G16 = host(wd.wd_net_apply(ctx, net, dev(R), bf16=True))
+    G32 = host(wd.wd_net_apply(ctx, net, dev(R)))
+    err = rel(G16, Y)
+    assert err <= (layers + 1) * 2.0 ** -8
+    assert err > 10 * rel(G32, Y)            # the activations really are BF16
+
+
+def test_net_bf16_preconditioned_solve(wd):
+    """precision 3 with a network: BF16 activations inside block BiCGGR still reach the FP64
+    answer (through the FP64-Jacobi fallback if the network stalls the method)."""
+    dims, L = (4, 4, 4, 4), 4
+    U = I.random_links(dims, 0.3, seed=0)
+    op = O.WilsonClover(U, dims, 0.115, 1.0)
+    B = I.z4_noise(dims, L, seed=1)
+    ctx = wd.wd_create(dev(U), dims, 0.115, 1.0)
+    net = wd.wd_net_create(4, 4, I.network_weights(4, 4, seed=7, noise=0.01))
+    X, info = wd.bbicggr_solve(ctx, dev(B), j=4, tol=1e-12, net=net, precision=3)
+    assert info["status"] == wd.WD_OK and info["fallbacks"] in (0, 1)
+    assert S.true_residual(op, B, host(X)).max() <= 1e-12
+    assert rel(host(X), S.solve(op, B, j=4, tol=1e-12).X) <= 1e-9
+
+
 def test_net_loss_gradient_and_adam_match_oracle(wd):
     dims, U, W, R, E = case(dims=(4, 4, 2, 4), L=2)
     ctx = wd.wd_create(dev(U), dims, 0.13, 1.0)

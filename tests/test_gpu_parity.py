@@ -290,7 +290,7 @@ def test_mixed_solve_8_8_8_16_near_critical(wd):
 
 def test_mixed_solve_falls_back_to_fp64_preconditioner_near_critical(wd):
     """Near the critical kappa the rounding of an FP32 preconditioner (a non-linear M) can stall
-    block BiCGGR, which needs a fixed linear M; the solve then continues from X with the FP64
+    block BiCGGR, which needs a fixed linear M; the solve then starts over from X_0 with the FP64
     preconditioner and still reaches the FP64 answer."""
     dims = (6, 6, 6, 6)
     links = I.random_links(dims, 0.2, seed=0)
@@ -307,8 +307,11 @@ def test_mixed_solve_falls_back_to_fp64_preconditioner_near_critical(wd):
     assert i0["fallbacks"] == 0
 
 
-@pytest.mark.parametrize("tile", [(1, 64, 0), (1, 128, 0), (1, 256, 0), (2, 64, 0), (2, 128, 0),
-                                  (2, 256, 0), (0, 128, 0), (2, 64, 8), (1, 64, 8)])
+TILES = [(1, 64, 0, 0), (1, 128, 0, 0), (1, 256, 0, 0), (2, 64, 0, 0), (2, 128, 0, 0),
+         (2, 256, 0, 0), (0, 128, 0, 0), (2, 64, 8, 0), (1, 64, 8, 0), (2, 64, 0, 1)]
+
+
+@pytest.mark.parametrize("tile", TILES)
 def test_fp32_sweep_tiles_match_oracle(wd, tile):
     """Every tile the autotuner may pick computes the same sweep."""
     dims, L = (3, 4, 5, 6), 6
@@ -327,9 +330,12 @@ def test_autotuner_picks_a_valid_tile(wd):
     ctx = wd.wd_create(dev(I.random_links(dims, 0.3, seed=0)), dims, 0.12, 1.0)
     assert wd.wd_tuned_tile(ctx, L) is None
     wd.jacobi_precond(ctx, dev(I.z4_noise(dims, L, seed=1)), 4, precision=1)
-    r, b, m = wd.wd_tuned_tile(ctx, L)
-    assert (r in (1, 2) and L % r == 0 and b in (64, 128, 256) and m in (0, 8)) or (r, b, m) == (0, 128, 0)
+    assert wd.wd_tuned_tile(ctx, L) in TILES
     with pytest.raises(wd.WDError):
         wd.wd_set_tile(ctx, 3, 2, 128)          # 2 does not divide L = 3
     with pytest.raises(wd.WDError):
         wd.wd_set_tile(ctx, 4, 2, 128, 8)       # the 128-register build takes 64-thread CTAs
+    with pytest.raises(wd.WDError):
+        wd.wd_set_tile(ctx, 4, 1, 64, 0, 1)     # the staged pipeline takes 2 RHS per thread
+    with pytest.raises(wd.WDError):
+        wd.wd_set_tile(ctx, 3, 2, 64, 0, 1)     # ... and an even L
