@@ -42,15 +42,20 @@ TOL = 1e-12
 # by the reference arm, which cannot run the full oracle solve, to scale its per-MVM time.
 WORKLOAD_ITERS = 36
 
-PRECISIONS = {"fp64": 0, "mixed": 1, "bf16": 3, "df": 4}   # bbicggr_opts.precision of each form
+PRECISIONS = {"fp64": 0, "mixed": 1, "bf16": 3, "df": 4, "df_dirs": 5}   # bbicggr_opts.precision
 FORM_NAMES = {"fp64": "plain FP64 Jacobi", "mixed": "mixed: FP32 Jacobi preconditioner",
               "bf16": "mixed: Jacobi preconditioner on BF16-stored blocks",
-              "df": "mixed: double-float Jacobi preconditioner (FP32 pairs, FP32 operator)"}
-# FP32 instructions per site and RHS of one double-float sweep: 8 hops x (12 two-sum additions
-# for the projection, 72 split products for the link, 24 additions into the sums) + the two 6x6
-# blocks (264 split products) + U + kappa H (24) + normalising the 24 stored reals (3 each) + the
-# row-2 rebuild of 8 links (30 each), with 11 instructions per split product and 8 per addition.
-DF_OPS = 8 * (12 * 8 + 72 * 11 + 24 * 8) + 264 * 11 + 24 * 11 + 24 * 3 + 8 * 30
+              "df": "mixed: double-float Jacobi preconditioner (FP32 pairs, FP32 operator)",
+              "df_dirs": "mixed: double-float preconditioner and direction recurrences"}
+# FP32 instructions per site and RHS of one double-float sweep, counting a split product (FP32
+# operator entry x FP32-pair value, added into a sum with two-sum) as 11, the first product of a sum
+# as 3 and a two-sum addition as 8.  Each of the 8 hops: 12 additions for the projection, the link
+# times two half-spinors (6 sums of 3 complex products: 6 x (2 x 3 + 2 x 11) + 12 x 4 x 11) and 24
+# additions into the sums; the row-2 rebuild of the 8 links (30 each); the two 6x6 blocks (12 rows
+# of 1 real and 5 complex products: 6 + 5 x 44 or 28 + 4 x 44 + 22 = 226); U + kappa H (24 split
+# products) and normalising the 24 stored reals (3 each).
+DF_OPS = 8 * (12 * 8 + 6 * (2 * 3 + 2 * 11) + 12 * 4 * 11 + 24 * 8) + 8 * 30 + 12 * 226 \
+    + 24 * 11 + 24 * 3
 FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12   # FP32 lane instructions per second (2070 MHz)
 METRIC = "time-to-solution at true resid 1e-12 for L RHS; Dslash HBM GB/s vs peak"
 FLOP_APPLY = 1824          # flop per site per RHS of A (1320 hopping + 504 clover)
@@ -330,7 +335,8 @@ def main():
                     help="fp64: the plain FP64 method (the default); mixed: FP32 Jacobi "
                          "preconditioner with the FP64 outer method; bf16: the preconditioner's "
                          "blocks stored in BF16, FP32 arithmetic; df: double-float (FP32-pair) "
-                         "preconditioner arithmetic")
+                         "preconditioner arithmetic; df_dirs: df and double-float direction "
+                         "recurrences")
     ap.add_argument("--fp32-tile", default="",
                     help="fix the FP32 sweep tile 'rhs_per_thread,block,min_blocks[,staged]' instead of "
                          "autotuning it (reproducible profiling)")
@@ -463,7 +469,8 @@ def main():
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    sweep_prec = {"fp64": "fp64", "mixed": "fp32", "bf16": "bf16", "df": "df"}[args.precision]
+    sweep_prec = {"fp64": "fp64", "mixed": "fp32", "bf16": "bf16", "df": "df",
+                  "df_dirs": "df"}[args.precision]
     per_kernel = {}
     for cls in ("dslash_jacobi_lp", "dslash_jacobi", "dslash_apply"):
         n, ms = prof.get(cls, (0, 0.0))
@@ -516,7 +523,8 @@ def main():
     out = {"metric": METRIC, "value": round(ms_step / 1e3, 6), "unit": "s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-           "dtype": {0: "f64", 1: "f64+f32", 3: "f64+f32(bf16 storage)", 4: "f64+df32x2"}[prec],
+           "dtype": {0: "f64", 1: "f64+f32", 3: "f64+f32(bf16 storage)", 4: "f64+df32x2",
+                     5: "f64+df32x2"}[prec],
            "data": "synthetic",
            "config": dict(config(args), sweep_tile=tile, link_reals=link_reals),
            "roofline": roofline,

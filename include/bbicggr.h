@@ -70,11 +70,14 @@ typedef struct {
                              (FP32-pair, ~48-bit) arithmetic on the FP32 pipes, with the X and R
                              updates and column norms still FP64; 3: as 1 with the
                              preconditioner's blocks (its copy of U and the sweep iterates) stored
-                             in BF16, arithmetic FP32.  In 1-3 the sweeps read 12-real links
-                             (rows 0 and 1, row 2 rebuilt) when wd_link_reals says 12 */
+                             in BF16, arithmetic FP32; 4: double-float sweeps -- the operator
+                             (links, A_D^{-1}, kappa) in FP32 and the spinors as FP32 pairs
+                             (~48 bits), so M is linear to ~1e-13; 5: as 4, and the direction
+                             recurrences in double-float as in 2.  In 1-5 the sweeps read 12-real
+                             links (rows 0 and 1, row 2 rebuilt) when wd_link_reals says 12 */
   double* history;        /* optional host array: max_i ||r_i||/||b_i|| after every R update */
   int history_len;        /* capacity of history (entries beyond it are dropped) */
-  int stall_window;       /* precision 1-3 only: when the max relative residual has not reached a new
+  int stall_window;       /* precision 1-5 only: when the max relative residual has not reached a new
                              minimum for this many iterations, or the low-precision run breaks
                              down or diverges, the solve starts over from X_0 with the FP64
                              preconditioner (block BiCGGR needs a fixed linear M, and the

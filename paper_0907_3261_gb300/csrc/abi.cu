@@ -141,12 +141,12 @@ namespace {
 enum { PM_F64 = 0, PM_F32 = 1, PM_NET = 2, PM_BF16 = 3, PM_DF = 4 };
 constexpr int DF_BLOCK = 128;   // threads per CTA of the double-float sweep
 inline int lp_storage(int mode) { return mode == PM_BF16 ? LP_BF16 : LP_F32; }
-// Mode for the public options: precision 1 and 2 sweep in FP32, 3 in BF16, 4 in double-float; a
-// network wins.
+// Mode for the public options: precision 1 and 2 sweep in FP32, 3 in BF16, 4 and 5 in
+// double-float; a network wins.
 inline int precond_mode(const bbicggr_opts& o) {
   if (o.net) return PM_NET;
   if (o.precision == 3) return PM_BF16;
-  if (o.precision == 4) return PM_DF;
+  if (o.precision == 4 || o.precision == 5) return PM_DF;
   return o.precision >= 1 ? PM_F32 : PM_F64;
 }
 
@@ -791,7 +791,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     set_err("invalid options");
     return WD_EINVAL;
   }
-  if (o.precision < 0 || o.precision > 4) { set_err("precision %d not in {0, ..., 4}", o.precision); return WD_EINVAL; }
+  if (o.precision < 0 || o.precision > 5) { set_err("precision %d not in {0, ..., 5}", o.precision); return WD_EINVAL; }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CHECK(ensure_workspace(c, L));
   const size_t bytes = block_bytes(c, L);
@@ -822,7 +822,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
 
   int status = WD_OK, iters = 0, restarts = 0, hist_n = 0, fallbacks = 0;
   int prec = precond_mode(o);
-  bool df = o.precision == 2;
+  bool df = o.precision == 2 || o.precision == 5;
   c->active_net = o.net;
   c->net_bf16 = o.net && o.precision == 3;
   const bool may_fall_back = prec != 0 && o.stall_window > 0;
@@ -1114,7 +1114,7 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     }
     const bbicggr_opts& o = jb.opts;
     if (o.maxit < 0 || !(o.div_thresh > 0.0) || o.stall_window < 0 ||
-        o.precision < 0 || o.precision > 4) {
+        o.precision < 0 || o.precision > 5) {
       set_err("job %d: invalid options", i);
       return WD_EINVAL;
     }
@@ -1160,7 +1160,7 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     c->active_net = jb.opts.net;
     c->net_bf16 = jb.opts.net && jb.opts.precision == 3;
     JobPtrs jp{static_cast<const double*>(jb.B), static_cast<double*>(jb.X), jb.L, jb.j,
-               precond_mode(jb.opts), jb.opts.precision == 2, jb.tol};
+               precond_mode(jb.opts), jb.opts.precision == 2 || jb.opts.precision == 5, jb.tol};
     rc = build_job(c, jp, G);
     c->prof.timing = timing;
   }

@@ -23,14 +23,12 @@ namespace {
 
 // ------------------------------------------------------------------ double-float helpers
 WD_DEV DF dfz() { return {0.f, 0.f}; }
-WD_DEV DF dneg(DF a) { return {-a.hi, -a.lo}; }
 // a + b, result unnormalised (hi carries the sum, lo the accumulated errors)
 WD_DEV DF dadd(DF a, DF b) {
   float s, t;
   two_sum(a.hi, b.hi, s, t);
   return {s, __fadd_rn(__fadd_rn(a.lo, b.lo), t)};
 }
-WD_DEV DF dsub(DF a, DF b) { return dadd(a, dneg(b)); }
 // acc + a b for an FP32 operator entry a: a b.hi = p + e exactly, a b.lo in FP32
 WD_DEV void dmac(DF& acc, float a, DF b) {
   const float p = __fmul_rn(a, b.hi);
@@ -42,25 +40,28 @@ WD_DEV void dmac(DF& acc, float a, DF b) {
   acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
 }
 
+// a b for an FP32 operator entry a, as the first term of a sum (no addition needed)
+WD_DEV DF dmul(float a, DF b) {
+  const float p = __fmul_rn(a, b.hi);
+  float e = __fmaf_rn(a, b.hi, -p);
+  return {p, __fmaf_rn(a, b.lo, e)};
+}
+
 using C = CDF;
 WD_DEV C cz() { return {dfz(), dfz()}; }
 WD_DEV C cadd(C a, C b) { return {dadd(a.re, b.re), dadd(a.im, b.im)}; }
-WD_DEV C csub(C a, C b) { return {dsub(a.re, b.re), dsub(a.im, b.im)}; }
-WD_DEV C cneg(C a) { return {dneg(a.re), dneg(a.im)}; }
-WD_DEV C cti(C a) { return {dneg(a.im), a.re}; }    // i a
-WD_DEV C ctmi(C a) { return {a.im, dneg(a.re)}; }   // -i a
 // acc + a b and acc + conj(a) b for an FP32 complex a
+WD_DEV C cmul1(Cx<float> a, C b) {   // a b, the first term of a sum
+  C acc = {dmul(a.re, b.re), dmul(a.re, b.im)};
+  dmac(acc.re, -a.im, b.im);
+  dmac(acc.im, a.im, b.re);
+  return acc;
+}
 WD_DEV void cmac(C& acc, Cx<float> a, C b) {
   dmac(acc.re, a.re, b.re);
   dmac(acc.re, -a.im, b.im);
   dmac(acc.im, a.re, b.im);
   dmac(acc.im, a.im, b.re);
-}
-WD_DEV void cmacj(C& acc, Cx<float> a, C b) {
-  dmac(acc.re, a.re, b.re);
-  dmac(acc.re, a.im, b.im);
-  dmac(acc.im, a.re, b.im);
-  dmac(acc.im, -a.im, b.re);
 }
 
 WD_DEV C ldq(const float4* p) {
@@ -82,20 +83,46 @@ WD_DEV TY* at(TY* y, size_t V, int L, int s, int k, int r) {
     return y + ((size_t)k * V + s) * L + r;
 }
 
-// G_mu d and G_mu^H w of the chiral basis (see dslash.cu) on double-float values.
-template <int MU>
-WD_DEV void gdown(C d0, C d1, C& g0, C& g1) {
-  if constexpr (MU == 0) { g0 = ctmi(d1); g1 = ctmi(d0); }
-  else if constexpr (MU == 1) { g0 = cneg(d1); g1 = d0; }
-  else if constexpr (MU == 2) { g0 = ctmi(d0); g1 = cti(d1); }
-  else { g0 = d0; g1 = d1; }
+// a + sg b for sg = +1 or -1, with the sign folded into FMAs: fma(sg, b, a) rounds a + sg b once,
+// exactly as an addition would, so this is two-sum on (a, sg b) at no extra cost.
+WD_DEV DF dadd_s(DF a, DF b, float sg) {
+  const float s = __fmaf_rn(sg, b.hi, a.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float t = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fmaf_rn(sg, b.hi, -bb));
+  return {s, __fadd_rn(__fmaf_rn(sg, b.lo, a.lo), t)};
 }
-template <int MU>
-WD_DEV void gup(C w0, C w1, C& g0, C& g1) {
-  if constexpr (MU == 0) { g0 = cti(w1); g1 = cti(w0); }
-  else if constexpr (MU == 1) { g0 = w1; g1 = cneg(w0); }
-  else if constexpr (MU == 2) { g0 = cti(w0); g1 = ctmi(w1); }
-  else { g0 = w0; g1 = w1; }
+// (re, im) or (im, re)
+WD_DEV C cswap(C z, bool swap) { return {swap ? z.im : z.re, swap ? z.re : z.im}; }
+
+// Spin structure of direction mu (chiral basis, see dslash.cu).  The hop multiplies
+// h = x_up - dir G_mu x_down by the link and adds w to the upper and -dir G_mu^H w to the lower
+// half.  Each G_mu is a signed, possibly re/im-swapped, diagonal or anti-diagonal of
+// {1, -1, i, -i}:  G_0 d = (-i d1, -i d0), G_1 d = (-d1, d0), G_2 d = (-i d0, i d1),
+// G_3 d = (d0, d1); G_0^H w = (i w1, i w0), G_1^H w = (w1, -w0), G_2^H w = (i w0, -i w1).
+// `cross` picks the anti-diagonal, `swap` multiplication by +-i, and the signs are those of the
+// (re, im) parts of slot 0 and slot 1, before the factor -dir.
+struct SpinDir {
+  bool cross, swap;
+  float dn[4], up[4];
+};
+WD_DEV SpinDir spin_dir(int mu, float mdir) {
+  SpinDir t;
+  t.cross = mu < 2;
+  t.swap = (mu & 1) == 0;
+  const float dn[4][4] = {{1, -1, 1, -1}, {-1, -1, 1, 1}, {1, -1, -1, 1}, {1, 1, 1, 1}};
+  const float up[4][4] = {{-1, 1, -1, 1}, {1, 1, -1, -1}, {-1, 1, 1, -1}, {1, 1, 1, 1}};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float a = dn[0][k], b = up[0][k];
+#pragma unroll
+    for (int m = 1; m < 4; ++m) {
+      a = mu == m ? dn[m][k] : a;
+      b = mu == m ? up[m][k] : b;
+    }
+    t.dn[k] = mdir * a;
+    t.up[k] = mdir * b;
+  }
+  return t;
 }
 
 // The 3x3 FP32 link with entry (a, b) at U[(3a + b) V]; row 2 read or rebuilt (SU(3)).
@@ -112,61 +139,80 @@ WD_DEV void link(const float2* __restrict__ U, size_t V, bool link12, Cx<float> 
   }
 }
 
-// Adds (1 - DIR g_mu) W x(s + DIR mu) to (au, ad); W = U_mu(s) (DIR = +1) or U_mu(s - mu)^H.
-template <int MU, int DIR>
-WD_DEV void hop(const float4* __restrict__ x, const float2* __restrict__ links, const Geom& g,
-                int s, const int c[4], int r, int L, bool link12, C au[2][3], C ad[2][3]) {
-  const int sn = neighbour(g, s, c, MU, DIR);
+// The hopping term H x at (s, r), accumulated into (au, ad) over the 8 directions in one rolled,
+// branch-free loop body: one copy of code serves every direction (which keeps the kernel inside
+// the instruction cache), the spin structure enters through load addresses, selects and signs
+// folded into the two-sum additions, and the backward link U_mu(s - mu)^H is conjugate-transposed
+// in registers.
+WD_DEV void hopping(const float4* __restrict__ x, const float2* __restrict__ links, const Geom& g,
+                    int s, const int c[4], int r, int L, bool link12, C au[2][3], C ad[2][3]) {
   const size_t V = (size_t)g.V;
-  const float4* base = x + (size_t)sn * L + r;
   const size_t cs = V * L;
-  C h0[3], h1[3];
+#pragma unroll 1
+  for (int d = 0; d < 8; ++d) {
+    const int mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    const int cm = mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
+    const int ext = g.d[mu], str = g.stride[mu];
+    const int sn = fwd ? (cm == ext - 1 ? s - (ext - 1) * str : s + str)
+                       : (cm == 0 ? s + (ext - 1) * str : s - str);
+    const SpinDir sd = spin_dir(mu, fwd ? -1.f : 1.f);
+    const float4* base = x + (size_t)sn * L + r;
+    const int k0 = sd.cross ? 9 : 6, k1 = sd.cross ? 6 : 9;   // lower-spin rows feeding slots 0, 1
+    C h0[3], h1[3];
 #pragma unroll
-  for (int col = 0; col < 3; ++col) {
-    const C u0 = ldq(base + (0 * 3 + col) * cs), u1 = ldq(base + (1 * 3 + col) * cs);
-    const C d0 = ldq(base + (2 * 3 + col) * cs), d1 = ldq(base + (3 * 3 + col) * cs);
-    C g0, g1;
-    gdown<MU>(d0, d1, g0, g1);
-    if constexpr (DIR > 0) { h0[col] = csub(u0, g0); h1[col] = csub(u1, g1); }
-    else { h0[col] = cadd(u0, g0); h1[col] = cadd(u1, g1); }
-  }
-  Cx<float> m[3][3];
-  link(links + (size_t)MU * 9 * V + (DIR > 0 ? s : sn), V, link12, m);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    C w0 = cz(), w1 = cz();
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      if constexpr (DIR > 0) { cmac(w0, m[a][b], h0[b]); cmac(w1, m[a][b], h1[b]); }
-      else { cmacj(w0, m[b][a], h0[b]); cmacj(w1, m[b][a], h1[b]); }
+    for (int col = 0; col < 3; ++col) {
+      const C u0 = ldq(base + (0 * 3 + col) * cs), u1 = ldq(base + (1 * 3 + col) * cs);
+      const C x0 = cswap(ldq(base + (k0 + col) * cs), sd.swap);
+      const C x1 = cswap(ldq(base + (k1 + col) * cs), sd.swap);
+      h0[col] = {dadd_s(u0.re, x0.re, sd.dn[0]), dadd_s(u0.im, x0.im, sd.dn[1])};
+      h1[col] = {dadd_s(u1.re, x1.re, sd.dn[2]), dadd_s(u1.im, x1.im, sd.dn[3])};
     }
-    C g0, g1;
-    gup<MU>(w0, w1, g0, g1);
-    au[0][a] = cadd(au[0][a], w0);
-    au[1][a] = cadd(au[1][a], w1);
-    if constexpr (DIR > 0) { ad[0][a] = csub(ad[0][a], g0); ad[1][a] = csub(ad[1][a], g1); }
-    else { ad[0][a] = cadd(ad[0][a], g0); ad[1][a] = cadd(ad[1][a], g1); }
+    Cx<float> m[3][3];
+    link(links + (size_t)mu * 9 * V + (fwd ? s : sn), V, link12, m);
+    if (!fwd) {   // W = m^H
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 3; ++b) {
+          const Cx<float> t = m[a][b];
+          m[a][b] = conj(m[b][a]);
+          m[b][a] = conj(t);
+        }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) m[a][a] = conj(m[a][a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      C w0 = cmul1(m[a][0], h0[0]), w1 = cmul1(m[a][0], h1[0]);
+#pragma unroll
+      for (int b = 1; b < 3; ++b) { cmac(w0, m[a][b], h0[b]); cmac(w1, m[a][b], h1[b]); }
+      au[0][a] = cadd(au[0][a], w0);
+      au[1][a] = cadd(au[1][a], w1);
+      const C y0 = cswap(sd.cross ? w1 : w0, sd.swap), y1 = cswap(sd.cross ? w0 : w1, sd.swap);
+      ad[0][a] = {dadd_s(ad[0][a].re, y0.re, sd.up[0]), dadd_s(ad[0][a].im, y0.im, sd.up[1])};
+      ad[1][a] = {dadd_s(ad[1][a].re, y1.re, sd.up[2]), dadd_s(ad[1][a].im, y1.im, sd.up[3])};
+    }
   }
 }
 
-// out = M v for a packed Hermitian 6x6 FP32 block with entries `stride` apart.
-WD_DEV void herm6(const float* __restrict__ m, size_t stride, const C v[6], C out[6]) {
+// Row i of a packed Hermitian 6x6 FP32 block (entries `stride` apart) times v: M_ij = l_ij below
+// the diagonal, conj(l_ji) above it, the real d_i on it (taken as a complex entry with a zero
+// imaginary part, which adds exact zeros and keeps the row branch-free).  Called in a rolled loop
+// over i.
+WD_DEV C herm6_row(const float* __restrict__ m, size_t stride, int i, const C v[6]) {
+  C acc;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const float d = __ldg(m + i * stride);
-    out[i] = cz();
-    dmac(out[i].re, d, v[i].re);
-    dmac(out[i].im, d, v[i].im);
+  for (int j = 0; j < 6; ++j) {
+    const int hi = j < i ? i : j, lo = j < i ? j : i;
+    const int t = hi == lo ? hi : tri_index(hi, lo);
+    const float re = __ldg(m + t * stride);
+    const float im = hi == lo ? 0.f : __ldg(m + (t + 1) * stride);
+    const Cx<float> l = cmake<float>(re, j > i ? -im : im);
+    if (j == 0) acc = cmul1(l, v[0]);
+    else cmac(acc, l, v[j]);
   }
-#pragma unroll
-  for (int i = 1; i < 6; ++i)
-#pragma unroll
-    for (int j = 0; j < i; ++j) {
-      const int t = tri_index(i, j);
-      const Cx<float> l = cmake<float>(__ldg(m + t * stride), __ldg(m + (t + 1) * stride));
-      cmac(out[i], l, v[j]);
-      cmacj(out[j], l, v[i]);
-    }
+  return acc;
 }
 
 // kappa h added to u (kappa an FP32 operator constant)
@@ -186,7 +232,6 @@ sweep_df_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4* 
   const int s = tid / L;
   const int r = tid - s * L;
   const size_t V = (size_t)g.V;
-  const bool l12 = link12 != 0;
   int c[4];
   site_coords(g, s, c);
   C au[2][3], ad[2][3];
@@ -194,26 +239,19 @@ sweep_df_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4* 
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) { au[a][b] = cz(); ad[a][b] = cz(); }
-  hop<0, +1>(x, links, g, s, c, r, L, l12, au, ad);
-  hop<0, -1>(x, links, g, s, c, r, L, l12, au, ad);
-  hop<1, +1>(x, links, g, s, c, r, L, l12, au, ad);
-  hop<1, -1>(x, links, g, s, c, r, L, l12, au, ad);
-  hop<2, +1>(x, links, g, s, c, r, L, l12, au, ad);
-  hop<2, -1>(x, links, g, s, c, r, L, l12, au, ad);
-  hop<3, +1>(x, links, g, s, c, r, L, l12, au, ad);
-  hop<3, -1>(x, links, g, s, c, r, L, l12, au, ad);
-#pragma unroll
+  hopping(x, links, g, s, c, r, L, link12 != 0, au, ad);
+#pragma unroll 1
   for (int ch = 0; ch < 2; ++ch) {
-    C vin[6], out[6];
+    C vin[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       const int k = ch * 6 + i;
       vin[i] = axpy(kappa, ch == 0 ? au[i / 3][i % 3] : ad[i / 3][i % 3],
                     ldq(u + ((size_t)k * V + s) * L + r));
     }
-    herm6(clov_inv + (size_t)ch * CLOV_REALS * V + s, V, vin, out);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) stq(at(y, V, L, s, ch * 6 + i, r), out[i]);
+    const float* m = clov_inv + (size_t)ch * CLOV_REALS * V + s;
+#pragma unroll 1
+    for (int i = 0; i < 6; ++i) stq(at(y, V, L, s, ch * 6 + i, r), herm6_row(m, V, i, vin));
   }
 }
 
@@ -228,21 +266,20 @@ site_inverse_df_kernel(const double* __restrict__ u, float4* __restrict__ u_df, 
   const int s = tid / L;
   const int r = tid - s * L;
   const size_t base = 2 * ((size_t)s * 12 * L + r);
-  C vin[2][6], out[2][6];
-#pragma unroll
-  for (int ch = 0; ch < 2; ++ch)
+#pragma unroll 1
+  for (int ch = 0; ch < 2; ++ch) {
+    C vin[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       const int k = ch * 6 + i;
-      vin[ch][i] = cdf_from(ldc(u + base + 2 * (size_t)(k * L)));
-      if (u_df) stq(at(u_df, (size_t)V, L, s, k, r), vin[ch][i]);
+      vin[i] = cdf_from(ldc(u + base + 2 * (size_t)(k * L)));
+      if (u_df) stq(at(u_df, (size_t)V, L, s, k, r), vin[i]);
     }
-  herm6(clov_inv + s, (size_t)V, vin[0], out[0]);
-  herm6(clov_inv + (size_t)CLOV_REALS * V + s, (size_t)V, vin[1], out[1]);
-#pragma unroll
-  for (int ch = 0; ch < 2; ++ch)
-#pragma unroll
-    for (int i = 0; i < 6; ++i) stq(at(y, (size_t)V, L, s, ch * 6 + i, r), out[ch][i]);
+    const float* m = clov_inv + (size_t)ch * CLOV_REALS * V + s;
+#pragma unroll 1
+    for (int i = 0; i < 6; ++i)
+      stq(at(y, (size_t)V, L, s, ch * 6 + i, r), herm6_row(m, (size_t)V, i, vin));
+  }
 }
 
 }  // namespace

@@ -198,15 +198,17 @@ def test_df_preconditioner_is_linear(wd, dims, L, j):
     assert nonlinearity(wd, ctx, x, y, j, 1) > 100 * DF_LINEARITY_TOL
 
 
+@pytest.mark.parametrize("precision", [4, 5])
 @pytest.mark.parametrize("B_kind,L,j", [("point", 4, 4), ("z4", 12, 4), ("z4", 3, 1)])
-def test_df_solve_matches_fp64_oracle(wd, B_kind, L, j):
+def test_df_solve_matches_fp64_oracle(wd, B_kind, L, j, precision):
+    """precision 4: double-float sweeps; 5: also double-float direction recurrences."""
     dims = (4, 4, 4, 4)
     links = I.random_links(dims, 0.3, seed=0)
     op = O.WilsonClover(links, dims, 0.115, 1.0)
     B = I.point_sources(dims, L) if B_kind == "point" else I.z4_noise(dims, L, seed=1)
     ref = S.solve(op, B, j=j, tol=1e-12)
     ctx = wd.wd_create(dev(links), dims, 0.115, 1.0)
-    Xg, info = wd.bbicggr_solve(ctx, dev(B), j=j, tol=1e-12, precision=4)
+    Xg, info = wd.bbicggr_solve(ctx, dev(B), j=j, tol=1e-12, precision=precision)
     Xg = host(Xg)
     assert info["status"] == wd.WD_OK and info["fallbacks"] == 0
     assert S.true_residual(op, B, Xg).max() <= TRUE_RES_TOL
