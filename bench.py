@@ -5,9 +5,12 @@ Workload (the paper's lattice, Sec. 3.1, with synthetic links in place of its co
 16^3 x 32 periodic lattice, links SU3proj(1 + 0.2 G) (seed 0), c_SW = 1.0, kappa = 0.134, L = 12
 Z4-noise sources (seed 1 + rank), Jacobi j = 12 (the paper's recommended L = 12, j >= 12, Sec. 3.3),
 X_0 = 0, R~_0 = R_0, tolerance 1e-12 on the recursive residual and then on the true residual.
-One step = one complete solve through the C-ABI, by default the plain FP64 method (--precision
-mixed: FP32 Jacobi preconditioner with the FP64 outer method; bf16: the same sweeps on BF16-stored
-blocks); the run also times the other forms on the same workload for comparison.  kappa = 0.134
+One step = one complete solve through the C-ABI.  By default the Jacobi sweeps run in double-float
+arithmetic (FP32 operator, spinors as FP32 pairs) and so do the direction recurrences, while the
+products with A, the X and R updates, the L x L solves and the true residual stay FP64
+(--precision df_dirs; fp64 is the plain FP64 method, df double-float sweeps only, mixed FP32 sweeps,
+bf16 FP32 sweeps on BF16-stored blocks).  The run also times the other forms on the same workload
+for comparison.  kappa = 0.134
 is the largest value of the 0.001-step sweep from 0.115 at which the L = 1, j = 0 solve still
 converges (660 iterations); at 0.135 it no longer does.
 
@@ -331,12 +334,12 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS),
-                    help="fp64: the plain FP64 method (the default); mixed: FP32 Jacobi "
+    ap.add_argument("--precision", default="df_dirs", choices=list(PRECISIONS),
+                    help="fp64: the plain FP64 method; mixed: FP32 Jacobi "
                          "preconditioner with the FP64 outer method; bf16: the preconditioner's "
                          "blocks stored in BF16, FP32 arithmetic; df: double-float (FP32-pair) "
-                         "preconditioner arithmetic; df_dirs: df and double-float direction "
-                         "recurrences")
+                         "preconditioner arithmetic; df_dirs (the default): df and double-float "
+                         "direction recurrences")
     ap.add_argument("--fp32-tile", default="",
                     help="fix the FP32 sweep tile 'rhs_per_thread,block,min_blocks[,staged]' instead of "
                          "autotuning it (reproducible profiling)")
@@ -420,6 +423,7 @@ def main():
     ms_total = maxr(e0.elapsed_time(e1))
     ms_step = ms_total / args.steps
     ok = all(i["status"] == wd.WD_OK and i["max_true_resid"] <= TOL for i in infos)
+    X_main = X.clone()   # this form's solution, compared per column with the FP64 form's below
 
     # ---- end to end through the C-ABI with pinned host buffers
     Xh = torch.zeros(B.shape, dtype=torch.complex128).pin_memory()
@@ -436,6 +440,7 @@ def main():
 
     # ---- the other precision forms on the same workload, for comparison (not the value)
     others = []
+    col_diff = None
     for oname, oprec in ([] if args.no_other_form else list(PRECISIONS.items())):
         if oprec == prec:
             continue
@@ -455,6 +460,9 @@ def main():
         torch.cuda.synchronize(dev)
         to = maxr(f0.elapsed_time(f1) / 2 / 1e3)
         ok = ok and all(i["status"] == wd.WD_OK for i in io)
+        if oprec == 0:   # ||X - X_fp64|| / ||X_fp64|| per column
+            Xf = X.reshape(-1, L_RHS)
+            col_diff = ((X_main.reshape(-1, L_RHS) - Xf).norm(dim=0) / Xf.norm(dim=0)).tolist()
         others.append({"form": FORM_NAMES[oname], "precision": oname,
                        "value": round(to, 6), "unit": "s", "iters": io[-1]["iters"],
                        "fallbacks": io[-1]["fallbacks"],
@@ -535,7 +543,10 @@ def main():
                      "mvm_paper": infos[-1]["mvm_paper"],
                      "max_true_resid": max(i["max_true_resid"] for i in infos),
                      "restarts": infos[-1]["restarts"],
-                     "fallbacks": infos[-1]["fallbacks"]},
+                     "fallbacks": infos[-1]["fallbacks"],
+                     "true_resid_per_column": [float(f"{v:.3e}") for v in infos[-1]["true_resid"]],
+                     "rel_diff_vs_fp64_per_column": (None if col_diff is None else
+                                                     [float(f"{v:.3e}") for v in col_diff])},
            "kernels": {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in prof.items() if n or ms}}
     if others:
         out["other_forms"] = others

@@ -101,27 +101,28 @@ WD_DEV C cswap(C z, bool swap) { return {swap ? z.im : z.re, swap ? z.re : z.im}
 // G_3 d = (d0, d1); G_0^H w = (i w1, i w0), G_1^H w = (w1, -w0), G_2^H w = (i w0, -i w1).
 // `cross` picks the anti-diagonal, `swap` multiplication by +-i, and the signs are those of the
 // (re, im) parts of slot 0 and slot 1, before the factor -dir.
+// Per direction d = 2 mu + (0 forward, 1 backward): the signs of (re, im) of slot 0 and slot 1 of
+// -dir G_mu x_down (dn) and of -dir G_mu^H w (up).  Read with a warp-uniform index.
+__constant__ float c_spin_dn[8][4] = {
+    {-1, 1, -1, 1}, {1, -1, 1, -1},     // mu 0: -i, -i
+    {1, 1, -1, -1}, {-1, -1, 1, 1},     // mu 1: -1, +1
+    {-1, 1, 1, -1}, {1, -1, -1, 1},     // mu 2: -i, +i
+    {-1, -1, -1, -1}, {1, 1, 1, 1}};    // mu 3: +1, +1
+__constant__ float c_spin_up[8][4] = {
+    {1, -1, 1, -1}, {-1, 1, -1, 1},     // mu 0: +i, +i
+    {-1, -1, 1, 1}, {1, 1, -1, -1},     // mu 1: +1, -1
+    {1, -1, -1, 1}, {-1, 1, 1, -1},     // mu 2: +i, -i
+    {-1, -1, -1, -1}, {1, 1, 1, 1}};    // mu 3: +1, +1
 struct SpinDir {
   bool cross, swap;
   float dn[4], up[4];
 };
-WD_DEV SpinDir spin_dir(int mu, float mdir) {
+WD_DEV SpinDir spin_dir(int d) {
   SpinDir t;
-  t.cross = mu < 2;
-  t.swap = (mu & 1) == 0;
-  const float dn[4][4] = {{1, -1, 1, -1}, {-1, -1, 1, 1}, {1, -1, -1, 1}, {1, 1, 1, 1}};
-  const float up[4][4] = {{-1, 1, -1, 1}, {1, 1, -1, -1}, {-1, 1, 1, -1}, {1, 1, 1, 1}};
+  t.cross = d < 4;
+  t.swap = ((d >> 1) & 1) == 0;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    float a = dn[0][k], b = up[0][k];
-#pragma unroll
-    for (int m = 1; m < 4; ++m) {
-      a = mu == m ? dn[m][k] : a;
-      b = mu == m ? up[m][k] : b;
-    }
-    t.dn[k] = mdir * a;
-    t.up[k] = mdir * b;
-  }
+  for (int k = 0; k < 4; ++k) { t.dn[k] = c_spin_dn[d][k]; t.up[k] = c_spin_up[d][k]; }
   return t;
 }
 
@@ -156,7 +157,7 @@ WD_DEV void hopping(const float4* __restrict__ x, const float2* __restrict__ lin
     const int ext = g.d[mu], str = g.stride[mu];
     const int sn = fwd ? (cm == ext - 1 ? s - (ext - 1) * str : s + str)
                        : (cm == 0 ? s + (ext - 1) * str : s - str);
-    const SpinDir sd = spin_dir(mu, fwd ? -1.f : 1.f);
+    const SpinDir sd = spin_dir(d);
     const float4* base = x + (size_t)sn * L + r;
     const int k0 = sd.cross ? 9 : 6, k1 = sd.cross ? 6 : 9;   // lower-spin rows feeding slots 0, 1
     C h0[3], h1[3];
@@ -200,15 +201,25 @@ WD_DEV void hopping(const float4* __restrict__ x, const float2* __restrict__ lin
 // the diagonal, conj(l_ji) above it, the real d_i on it (taken as a complex entry with a zero
 // imaginary part, which adds exact zeros and keeps the row branch-free).  Called in a rolled loop
 // over i.
+// Offset of the real part of M_ij in the packed block (the diagonal reals first, then the
+// strictly-lower pairs), and the sign of the imaginary part: 0 on the diagonal (no imaginary part),
+// +1 below it, -1 above it (conjugate of the lower entry).
+__constant__ int c_h6_off[6][6] = {
+    {0, 6, 8, 12, 18, 26}, {6, 1, 10, 14, 20, 28}, {8, 10, 2, 16, 22, 30},
+    {12, 14, 16, 3, 24, 32}, {18, 20, 22, 24, 4, 34}, {26, 28, 30, 32, 34, 5}};
+__constant__ float c_h6_sgn[6][6] = {
+    {0, -1, -1, -1, -1, -1}, {1, 0, -1, -1, -1, -1}, {1, 1, 0, -1, -1, -1},
+    {1, 1, 1, 0, -1, -1}, {1, 1, 1, 1, 0, -1}, {1, 1, 1, 1, 1, 0}};
+
 WD_DEV C herm6_row(const float* __restrict__ m, size_t stride, int i, const C v[6]) {
   C acc;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
-    const int hi = j < i ? i : j, lo = j < i ? j : i;
-    const int t = hi == lo ? hi : tri_index(hi, lo);
+    const int t = c_h6_off[i][j];
+    const float sg = c_h6_sgn[i][j];
     const float re = __ldg(m + t * stride);
-    const float im = hi == lo ? 0.f : __ldg(m + (t + 1) * stride);
-    const Cx<float> l = cmake<float>(re, j > i ? -im : im);
+    const float im = __ldg(m + (t + (sg != 0.f)) * stride);   // the diagonal reads itself twice
+    const Cx<float> l = cmake<float>(re, sg * im);
     if (j == 0) acc = cmul1(l, v[0]);
     else cmac(acc, l, v[j]);
   }
