@@ -247,7 +247,8 @@ const char* wd_profile_name(int kernel_class);
 int wd_tuned_tile(const wd_ctx* ctx, int L, int precision, int* rhs_per_thread, int* block,
                   int* min_blocks, int* staged);
 /* Sets that tile by hand instead: rhs_per_thread 1 or 2 dividing L with block 64, 128 or 256,
- * min_blocks 0 (or 8 with block 64) and staged 0; rhs_per_thread 0 with block 128 (the stencil of
+ * min_blocks 0 (or, with block 64, 8, or 12 with one RHS per thread: at most 80 registers) and
+ * staged 0; rhs_per_thread 0 with block 128 (the stencil of
  * every (site, rhs) pair split over two warps); or staged 1 with rhs_per_thread 2, block 64 and
  * min_blocks 0. */
 int wd_set_tile(wd_ctx* ctx, int L, int precision, int rhs_per_thread, int block, int min_blocks,

@@ -242,7 +242,7 @@ int ensure_workspace(wd_ctx* c, int L) {
 int autotune_lp(wd_ctx* c, int storage, int L, cudaStream_t s) {
   static const int cand[][4] = {{1, 64, 0, 0},  {1, 128, 0, 0}, {1, 256, 0, 0}, {2, 64, 0, 0},
                                 {2, 128, 0, 0}, {2, 256, 0, 0}, {0, 128, 0, 0}, {2, 64, 8, 0},
-                                {2, 64, 0, 1}};
+                                {2, 64, 0, 1},  {1, 64, 12, 0}};
   const size_t bytes = (size_t)c->op.g.V * 12 * L * lp_elem_bytes(storage);
   void* u_lp = c->blk32[0].p;
   void* a = c->blk32[1].p;
@@ -663,7 +663,8 @@ int wd_set_tile(wd_ctx* c, int L, int precision, int rhs_per_thread, int block, 
   int st;
   CHECK(tile_storage(precision, &st));
   const bool split = rhs_per_thread == 0 && block == 128 && min_blocks == 0;
-  const bool capped = min_blocks == 8 && block == 64 && rhs_per_thread != 0;
+  const bool capped = block == 64 && ((min_blocks == 8 && rhs_per_thread != 0) ||
+                                      (min_blocks == 12 && rhs_per_thread == 1));
   const bool pipe = staged == 1 && rhs_per_thread == 2 && block == 64 && min_blocks == 0 && L % 2 == 0;
   if ((staged != 0 && !pipe) ||
       (!staged && !split && ((rhs_per_thread != 1 && rhs_per_thread != 2) || L % rhs_per_thread != 0 ||

@@ -495,6 +495,9 @@ cudaError_t launch_sweep_r(const Op& op, const E* g_in, const E* u_lp, TY* out, 
   if (min_blocks == 8 && block == 64)    // at most 128 registers: 16 warps per SM
     sweep_kernel<R, E, TY, 64, 8><<<grid, block, 0, st>>>(g_in, out, u_lp, links, op.clov_inv32,
                                                           op.g, L, (float)op.kappa, op.link12);
+  else if (min_blocks == 12 && block == 64 && R == 1)   // at most 80 registers: 24 warps per SM
+    sweep_kernel<1, E, TY, 64, 12><<<grid, block, 0, st>>>(g_in, out, u_lp, links, op.clov_inv32,
+                                                           op.g, L, (float)op.kappa, op.link12);
   else
     sweep_kernel<R, E, TY, 256, 1><<<grid, block, 0, st>>>(g_in, out, u_lp, links, op.clov_inv32,
                                                            op.g, L, (float)op.kappa, op.link12);

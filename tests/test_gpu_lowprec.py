@@ -94,7 +94,8 @@ def test_jacobi_bf16_matches_oracle(wd, j, dims, L):
 
 
 TILES = [(1, 64, 0, 0), (1, 128, 0, 0), (1, 256, 0, 0), (2, 64, 0, 0), (2, 128, 0, 0),
-         (2, 256, 0, 0), (0, 128, 0, 0), (2, 64, 8, 0), (1, 64, 8, 0), (2, 64, 0, 1)]
+         (2, 256, 0, 0), (0, 128, 0, 0), (2, 64, 8, 0), (1, 64, 8, 0), (2, 64, 0, 1),
+         (1, 64, 12, 0)]
 
 
 @pytest.mark.parametrize("tile", TILES)

@@ -308,7 +308,8 @@ def test_mixed_solve_falls_back_to_fp64_preconditioner_near_critical(wd):
 
 
 TILES = [(1, 64, 0, 0), (1, 128, 0, 0), (1, 256, 0, 0), (2, 64, 0, 0), (2, 128, 0, 0),
-         (2, 256, 0, 0), (0, 128, 0, 0), (2, 64, 8, 0), (1, 64, 8, 0), (2, 64, 0, 1)]
+         (2, 256, 0, 0), (0, 128, 0, 0), (2, 64, 8, 0), (1, 64, 8, 0), (2, 64, 0, 1),
+         (1, 64, 12, 0)]
 
 
 @pytest.mark.parametrize("tile", TILES)
