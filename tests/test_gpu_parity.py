@@ -242,6 +242,28 @@ def test_full_size_16_16_16_32(wd):
         assert S.true_residual(op, B, host(Xg)).max() <= TRUE_RES_TOL
 
 
+def test_bench_workload_double_float_forms(wd):
+    """The bench workload itself (16^3 x 32, kappa = 0.134 near the critical kappa, L = 12, j = 12)
+    in the plain FP64 form and the two double-float forms: every column's true residual,
+    recomputed by the oracle, is <= 1e-12, the double-float forms need no fallback, and their
+    solutions agree with the FP64 form's column by column."""
+    dims, kappa = (16, 16, 16, 32), 0.134
+    links = I.random_links(dims, 0.2, seed=0)
+    op = O.WilsonClover(links, dims, kappa, 1.0)
+    ctx = wd.wd_create(dev(links), dims, kappa, 1.0)
+    B = I.z4_noise(dims, 12, seed=1)
+    sols = {}
+    for precision in (0, 4, 5):
+        Xg, info = wd.bbicggr_solve(ctx, dev(B), j=12, tol=1e-12, precision=precision)
+        assert info["status"] == wd.WD_OK and info["fallbacks"] == 0
+        sols[precision] = host(Xg)
+        assert S.true_residual(op, B, sols[precision]).max() <= TRUE_RES_TOL
+    ref = sols[0].reshape(-1, 12)
+    for precision in (4, 5):
+        d = np.linalg.norm(sols[precision].reshape(-1, 12) - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        assert d.max() <= SOLVE_X_TOL
+
+
 # ---------------------------------------------------------------- FP32 preconditioner (precision 1)
 @pytest.mark.parametrize("j", [1, 2, 5, 12])
 @pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 4), ((3, 4, 5, 6), 7), ((8, 8, 8, 16), 12)])
