@@ -527,7 +527,8 @@ def main():
     roofline["stencil_kernels"] = per_kernel
 
     launches = sum(n for k, (n, _) in prof.items())
-    tile = wd.wd_tuned_tile(ctx, L_RHS, precision=3 if prec == 3 else 1) if prec in (1, 2, 3) else None
+    tile = (wd.wd_tuned_tile(ctx, L_RHS, precision={1: 1, 2: 1, 3: 3, 4: 4, 5: 4}[prec])
+            if prec else None)
     out = {"metric": METRIC, "value": round(ms_step / 1e3, 6), "unit": "s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,

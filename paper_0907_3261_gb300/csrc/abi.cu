@@ -117,13 +117,13 @@ struct wd_ctx {
   DevBuf stage_in, stage_out;
   // low-precision preconditioner blocks: U and two sweep buffers (sized for FP32 elements)
   DevBuf blk32[3];
-  // autotuned tile of the low-precision sweep per storage (LP_F32, LP_BF16) and L: RHS per
+  // autotuned tile of the low-precision sweep per storage (LP_F32, LP_BF16, LP_DF) and L: RHS per
   // thread, threads per CTA, min CTAs per SM, shared-memory staging
-  int tile_r[2][WD_LMAX + 1] = {};
-  int tile_block[2][WD_LMAX + 1] = {};
-  int tile_minb[2][WD_LMAX + 1] = {};
-  int tile_staged[2][WD_LMAX + 1] = {};
-  bool tile_set[2][WD_LMAX + 1] = {};
+  int tile_r[3][WD_LMAX + 1] = {};
+  int tile_block[3][WD_LMAX + 1] = {};
+  int tile_minb[3][WD_LMAX + 1] = {};
+  int tile_staged[3][WD_LMAX + 1] = {};
+  bool tile_set[3][WD_LMAX + 1] = {};
   bool links_su3 = false;         // the links are special unitary to LINK12_TOL
   wd_net* active_net = nullptr;   // learned preconditioner of the running solve (mode 2)
   bool net_bf16 = false;          // ... with its activations stored in BF16 (precision 3)
@@ -139,7 +139,7 @@ namespace {
 // Preconditioner modes of precondition(): FP64 sweeps, FP32-storage sweeps, the learned network,
 // BF16-storage sweeps, double-float sweeps.
 enum { PM_F64 = 0, PM_F32 = 1, PM_NET = 2, PM_BF16 = 3, PM_DF = 4 };
-constexpr int DF_BLOCK = 128;   // threads per CTA of the double-float sweep
+
 inline int lp_storage(int mode) { return mode == PM_BF16 ? LP_BF16 : LP_F32; }
 // Mode for the public options: precision 1 and 2 sweep in FP32, 3 in BF16, 4 and 5 in
 // double-float; a network wins.
@@ -281,10 +281,43 @@ int autotune_lp(wd_ctx* c, int storage, int L, cudaStream_t s) {
   return WD_OK;
 }
 
-// Double-float blocks take 16 bytes per complex number, like FP64 blocks.
-int ensure_workspace_df(wd_ctx* c, int L) {
+// Double-float blocks take 16 bytes per complex number, like FP64 blocks.  The double-float sweep
+// takes 1 or 2 RHS per thread in 128-thread CTAs; the faster for this lattice and L is kept.
+int ensure_workspace_df(wd_ctx* c, int L, cudaStream_t s) {
   const size_t bytes = (size_t)c->op.g.V * 12 * L * 16;
   for (auto& b : c->blk32) CHECK(b.ensure(bytes));
+  if (c->tile_set[LP_DF][L]) return WD_OK;
+  void* u_df = c->blk32[0].p;
+  void* a = c->blk32[1].p;
+  void* b = c->blk32[2].p;
+  CU(cudaMemsetAsync(u_df, 0, bytes, s));
+  CU(cudaMemsetAsync(a, 0, bytes, s));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_r = 1;
+  cudaError_t err = cudaSuccess;
+  for (int r = 1; r <= 2 && err == cudaSuccess; ++r) {
+    if (L % r != 0) continue;
+    err = launch_jacobi_df(c->op, a, u_df, b, nullptr, L, r, 128, s);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
+      err = launch_jacobi_df(c->op, a, u_df, b, nullptr, L, r, 128, s);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && ms < best) { best = ms; best_r = r; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CU(err);
+  c->tile_r[LP_DF][L] = best_r;
+  c->tile_block[LP_DF][L] = 128;
+  c->tile_minb[LP_DF][L] = 0;
+  c->tile_staged[LP_DF][L] = 0;
+  c->tile_set[LP_DF][L] = true;
   return WD_OK;
 }
 
@@ -334,7 +367,7 @@ int precondition(wd_ctx* c, const double* R, double* a, double* b, double** res,
       LAUNCH(WD_K_SITE_INV, 1, launch_site_inverse_df(op, R, nullptr, nullptr, a, L, s));
       return WD_OK;
     }
-    CHECK(ensure_workspace_df(c, L));
+    CHECK(ensure_workspace_df(c, L, s));
     void* u_df = c->blk32[0].p;
     void* cur = c->blk32[1].p;
     void* nxt = c->blk32[2].p;
@@ -343,7 +376,7 @@ int precondition(wd_ctx* c, const double* R, double* a, double* b, double** res,
       const bool last = i == j - 1;
       LAUNCH(WD_K_JACOBI_LP, 1,
              launch_jacobi_df(op, cur, u_df, last ? nullptr : nxt, last ? a : nullptr, L,
-                              DF_BLOCK, s));
+                              c->tile_r[LP_DF][L], c->tile_block[LP_DF][L], s));
       if (hop_count) ++*hop_count;
       void* t = cur;
       cur = nxt;
@@ -652,7 +685,8 @@ const char* wd_profile_name(int cls) {
 static int tile_storage(int precision, int* storage) {
   if (precision == 1) { *storage = LP_F32; return WD_OK; }
   if (precision == 3) { *storage = LP_BF16; return WD_OK; }
-  set_err("precision %d has no sweep tile (1 = FP32, 3 = BF16 storage)", precision);
+  if (precision == 4) { *storage = LP_DF; return WD_OK; }
+  set_err("precision %d has no sweep tile (1 = FP32, 3 = BF16 storage, 4 = double-float)", precision);
   return WD_EINVAL;
 }
 
@@ -662,6 +696,20 @@ int wd_set_tile(wd_ctx* c, int L, int precision, int rhs_per_thread, int block, 
   CHECK(check_L(L));
   int st;
   CHECK(tile_storage(precision, &st));
+  if (st == LP_DF) {   // 1 or 2 RHS per thread, 128 threads
+    if ((rhs_per_thread != 1 && rhs_per_thread != 2) || L % rhs_per_thread != 0 || block != 128 ||
+        min_blocks != 0 || staged != 0) {
+      set_err("double-float tile (%d RHS/thread, %d threads) not available for L = %d",
+              rhs_per_thread, block, L);
+      return WD_EINVAL;
+    }
+    c->tile_r[st][L] = rhs_per_thread;
+    c->tile_block[st][L] = block;
+    c->tile_minb[st][L] = 0;
+    c->tile_staged[st][L] = 0;
+    c->tile_set[st][L] = true;
+    return WD_OK;
+  }
   const bool split = rhs_per_thread == 0 && block == 128 && min_blocks == 0;
   const bool capped = block == 64 && ((min_blocks == 8 && rhs_per_thread != 0) ||
                                       (min_blocks == 12 && rhs_per_thread == 1));
@@ -1128,7 +1176,7 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     const int mode = precond_mode(jb.opts);
     if ((mode == PM_F32 || mode == PM_BF16) && jb.j >= 2)
       CHECK(ensure_workspace_lp(c, lp_storage(mode), jb.L, s));
-    if (mode == PM_DF && jb.j >= 2) CHECK(ensure_workspace_df(c, jb.L));
+    if (mode == PM_DF && jb.j >= 2) CHECK(ensure_workspace_df(c, jb.L, s));
     if (mode == PM_NET) CHECK(wd_net_prepare(c, jb.opts.net, jb.L));
     if (!c->gctl) CU(cudaMalloc(&c->gctl, sizeof(GraphCtl)));
     const int hl = jb.opts.history ? jb.opts.history_len : 0;

@@ -40,7 +40,7 @@ cudaError_t launch_site_inverse_f64(const Op& op, const double* u, double* g_out
 // blocks (u_lp, g_lp) are component-major, [spin*3+colour][site][rhs], one complex number per
 // element: float2 (LP_F32) or two packed BF16 numbers (LP_BF16); FP64 blocks are site-major.
 // Exactly one of g_lp / g64 is non-null.
-enum { LP_F32 = 0, LP_BF16 = 1 };
+enum { LP_F32 = 0, LP_BF16 = 1, LP_DF = 2 };   // LP_DF: the double-float sweep's tile table
 constexpr size_t lp_elem_bytes(int storage) { return storage == LP_BF16 ? 4 : 8; }
 
 // FP32 component-major links and A_D^{-1}; sets *not_su3 (device) when some link is not special
@@ -73,8 +73,9 @@ cudaError_t launch_jacobi_bf16_tiled(const Op& op, const void* g_in, const void*
 // blocks are component-major with one float4 (re.hi, re.lo, im.hi, im.lo) per complex number.
 cudaError_t launch_site_inverse_df(const Op& op, const double* u, void* u_df, void* g_df,
                                    double* g64, int L, cudaStream_t st);
+// One sweep with 1 or 2 RHS per thread (dividing L) and `block` (64 or 128) threads per CTA.
 cudaError_t launch_jacobi_df(const Op& op, const void* g_in, const void* u_df, void* g_df,
-                             double* g64, int L, int block, cudaStream_t st);
+                             double* g64, int L, int rhs_per_thread, int block, cudaStream_t st);
 
 // ---- clover.cu
 // Builds clov and clov_inv from links; *singular_dev receives 1 if some 6x6 block is singular.

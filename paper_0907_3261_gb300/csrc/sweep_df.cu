@@ -11,7 +11,7 @@
 // FP32 rate, this is several times faster than FP64 sweeps.
 //
 // Blocks are component-major, [spin*3+colour][site][rhs], one float4 (re.hi, re.lo, im.hi,
-// im.lo) per complex number; one thread owns one (site, rhs) pair.  The first sweep converts the
+// im.lo) per complex number; one thread owns one site and 1 or 2 consecutive right-hand sides.  The first sweep converts the
 // FP64 right-hand side and stores its double-float copy; the last writes FP64 site-major.
 #include <type_traits>
 
@@ -145,8 +145,10 @@ WD_DEV void link(const float2* __restrict__ U, size_t V, bool link12, Cx<float> 
 // the instruction cache), the spin structure enters through load addresses, selects and signs
 // folded into the two-sum additions, and the backward link U_mu(s - mu)^H is conjugate-transposed
 // in registers.
+template <int R>
 WD_DEV void hopping(const float4* __restrict__ x, const float2* __restrict__ links, const Geom& g,
-                    int s, const int c[4], int r, int L, bool link12, C au[2][3], C ad[2][3]) {
+                    int s, const int c[4], int r, int L, bool link12, C au[R][2][3],
+                    C ad[R][2][3]) {
   const size_t V = (size_t)g.V;
   const size_t cs = V * L;
 #pragma unroll 1
@@ -160,15 +162,17 @@ WD_DEV void hopping(const float4* __restrict__ x, const float2* __restrict__ lin
     const SpinDir sd = spin_dir(d);
     const float4* base = x + (size_t)sn * L + r;
     const int k0 = sd.cross ? 9 : 6, k1 = sd.cross ? 6 : 9;   // lower-spin rows feeding slots 0, 1
-    C h0[3], h1[3];
+    C h0[R][3], h1[R][3];
 #pragma unroll
-    for (int col = 0; col < 3; ++col) {
-      const C u0 = ldq(base + (0 * 3 + col) * cs), u1 = ldq(base + (1 * 3 + col) * cs);
-      const C x0 = cswap(ldq(base + (k0 + col) * cs), sd.swap);
-      const C x1 = cswap(ldq(base + (k1 + col) * cs), sd.swap);
-      h0[col] = {dadd_s(u0.re, x0.re, sd.dn[0]), dadd_s(u0.im, x0.im, sd.dn[1])};
-      h1[col] = {dadd_s(u1.re, x1.re, sd.dn[2]), dadd_s(u1.im, x1.im, sd.dn[3])};
-    }
+    for (int col = 0; col < 3; ++col)
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const C u0 = ldq(base + (0 * 3 + col) * cs + q), u1 = ldq(base + (1 * 3 + col) * cs + q);
+        const C x0 = cswap(ldq(base + (k0 + col) * cs + q), sd.swap);
+        const C x1 = cswap(ldq(base + (k1 + col) * cs + q), sd.swap);
+        h0[q][col] = {dadd_s(u0.re, x0.re, sd.dn[0]), dadd_s(u0.im, x0.im, sd.dn[1])};
+        h1[q][col] = {dadd_s(u1.re, x1.re, sd.dn[2]), dadd_s(u1.im, x1.im, sd.dn[3])};
+      }
     Cx<float> m[3][3];
     link(links + (size_t)mu * 9 * V + (fwd ? s : sn), V, link12, m);
     if (!fwd) {   // W = m^H
@@ -184,16 +188,18 @@ WD_DEV void hopping(const float4* __restrict__ x, const float2* __restrict__ lin
       for (int a = 0; a < 3; ++a) m[a][a] = conj(m[a][a]);
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      C w0 = cmul1(m[a][0], h0[0]), w1 = cmul1(m[a][0], h1[0]);
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 1; b < 3; ++b) { cmac(w0, m[a][b], h0[b]); cmac(w1, m[a][b], h1[b]); }
-      au[0][a] = cadd(au[0][a], w0);
-      au[1][a] = cadd(au[1][a], w1);
-      const C y0 = cswap(sd.cross ? w1 : w0, sd.swap), y1 = cswap(sd.cross ? w0 : w1, sd.swap);
-      ad[0][a] = {dadd_s(ad[0][a].re, y0.re, sd.up[0]), dadd_s(ad[0][a].im, y0.im, sd.up[1])};
-      ad[1][a] = {dadd_s(ad[1][a].re, y1.re, sd.up[2]), dadd_s(ad[1][a].im, y1.im, sd.up[3])};
-    }
+      for (int q = 0; q < R; ++q) {
+        C w0 = cmul1(m[a][0], h0[q][0]), w1 = cmul1(m[a][0], h1[q][0]);
+#pragma unroll
+        for (int b = 1; b < 3; ++b) { cmac(w0, m[a][b], h0[q][b]); cmac(w1, m[a][b], h1[q][b]); }
+        au[q][0][a] = cadd(au[q][0][a], w0);
+        au[q][1][a] = cadd(au[q][1][a], w1);
+        const C y0 = cswap(sd.cross ? w1 : w0, sd.swap), y1 = cswap(sd.cross ? w0 : w1, sd.swap);
+        ad[q][0][a] = {dadd_s(ad[q][0][a].re, y0.re, sd.up[0]), dadd_s(ad[q][0][a].im, y0.im, sd.up[1])};
+        ad[q][1][a] = {dadd_s(ad[q][1][a].re, y1.re, sd.up[2]), dadd_s(ad[q][1][a].im, y1.im, sd.up[3])};
+      }
   }
 }
 
@@ -211,8 +217,9 @@ __constant__ float c_h6_sgn[6][6] = {
     {0, -1, -1, -1, -1, -1}, {1, 0, -1, -1, -1, -1}, {1, 1, 0, -1, -1, -1},
     {1, 1, 1, 0, -1, -1}, {1, 1, 1, 1, 0, -1}, {1, 1, 1, 1, 1, 0}};
 
-WD_DEV C herm6_row(const float* __restrict__ m, size_t stride, int i, const C v[6]) {
-  C acc;
+template <int R>
+WD_DEV void herm6_row(const float* __restrict__ m, size_t stride, int i, const C v[R][6],
+                      C acc[R]) {
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     const int t = c_h6_off[i][j];
@@ -220,10 +227,12 @@ WD_DEV C herm6_row(const float* __restrict__ m, size_t stride, int i, const C v[
     const float re = __ldg(m + t * stride);
     const float im = __ldg(m + (t + (sg != 0.f)) * stride);   // the diagonal reads itself twice
     const Cx<float> l = cmake<float>(re, sg * im);
-    if (j == 0) acc = cmul1(l, v[0]);
-    else cmac(acc, l, v[j]);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      if (j == 0) acc[q] = cmul1(l, v[q][0]);
+      else cmac(acc[q], l, v[q][j]);
+    }
   }
-  return acc;
 }
 
 // kappa h added to u (kappa an FP32 operator constant)
@@ -233,36 +242,48 @@ WD_DEV C axpy(float kappa, C h, C u) {
   return u;
 }
 
-template <typename TY>
-__global__ void __launch_bounds__(128)
+// R consecutive right-hand sides per thread (R = 1 or 2 dividing L); the links, the spin
+// constants and the clover entries serve all R.
+template <int R, typename TY>
+__global__ void __launch_bounds__(128, R == 1 ? 4 : 2)
 sweep_df_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4* __restrict__ u,
                 const float2* __restrict__ links, const float* __restrict__ clov_inv, Geom g,
                 int L, float kappa, int link12) {
+  const int groups = L / R;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= g.V * L) return;
-  const int s = tid / L;
-  const int r = tid - s * L;
+  if (tid >= g.V * groups) return;
+  const int s = tid / groups;
+  const int r = (tid - s * groups) * R;
   const size_t V = (size_t)g.V;
   int c[4];
   site_coords(g, s, c);
-  C au[2][3], ad[2][3];
+  C au[R][2][3], ad[R][2][3];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int q = 0; q < R; ++q)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) { au[a][b] = cz(); ad[a][b] = cz(); }
-  hopping(x, links, g, s, c, r, L, link12 != 0, au, ad);
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) { au[q][a][b] = cz(); ad[q][a][b] = cz(); }
+  hopping<R>(x, links, g, s, c, r, L, link12 != 0, au, ad);
 #pragma unroll 1
   for (int ch = 0; ch < 2; ++ch) {
-    C vin[6];
+    C vin[R][6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      const int k = ch * 6 + i;
-      vin[i] = axpy(kappa, ch == 0 ? au[i / 3][i % 3] : ad[i / 3][i % 3],
-                    ldq(u + ((size_t)k * V + s) * L + r));
-    }
+    for (int q = 0; q < R; ++q)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const int k = ch * 6 + i;
+        vin[q][i] = axpy(kappa, ch == 0 ? au[q][i / 3][i % 3] : ad[q][i / 3][i % 3],
+                         ldq(u + ((size_t)k * V + s) * L + r + q));
+      }
     const float* m = clov_inv + (size_t)ch * CLOV_REALS * V + s;
 #pragma unroll 1
-    for (int i = 0; i < 6; ++i) stq(at(y, V, L, s, ch * 6 + i, r), herm6_row(m, V, i, vin));
+    for (int i = 0; i < 6; ++i) {
+      C out[R];
+      herm6_row<R>(m, V, i, vin, out);
+#pragma unroll
+      for (int q = 0; q < R; ++q) stq(at(y, V, L, s, ch * 6 + i, r + q), out[q]);
+    }
   }
 }
 
@@ -279,17 +300,20 @@ site_inverse_df_kernel(const double* __restrict__ u, float4* __restrict__ u_df, 
   const size_t base = 2 * ((size_t)s * 12 * L + r);
 #pragma unroll 1
   for (int ch = 0; ch < 2; ++ch) {
-    C vin[6];
+    C vin[1][6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       const int k = ch * 6 + i;
-      vin[i] = cdf_from(ldc(u + base + 2 * (size_t)(k * L)));
-      if (u_df) stq(at(u_df, (size_t)V, L, s, k, r), vin[i]);
+      vin[0][i] = cdf_from(ldc(u + base + 2 * (size_t)(k * L)));
+      if (u_df) stq(at(u_df, (size_t)V, L, s, k, r), vin[0][i]);
     }
     const float* m = clov_inv + (size_t)ch * CLOV_REALS * V + s;
 #pragma unroll 1
-    for (int i = 0; i < 6; ++i)
-      stq(at(y, (size_t)V, L, s, ch * 6 + i, r), herm6_row(m, (size_t)V, i, vin));
+    for (int i = 0; i < 6; ++i) {
+      C out[1];
+      herm6_row<1>(m, (size_t)V, i, vin, out);
+      stq(at(y, (size_t)V, L, s, ch * 6 + i, r), out[0]);
+    }
   }
 }
 
@@ -307,19 +331,30 @@ cudaError_t launch_site_inverse_df(const Op& op, const double* u, void* u_df, vo
   return cudaGetLastError();
 }
 
-cudaError_t launch_jacobi_df(const Op& op, const void* g_in, const void* u_df, void* g_df,
-                             double* g64, int L, int block, cudaStream_t st) {
-  if (block != 64 && block != 128) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)(((long long)op.g.V * L + block - 1) / block);
-  const float4* x = static_cast<const float4*>(g_in);
-  const float4* u = static_cast<const float4*>(u_df);
+namespace {
+template <int R>
+cudaError_t launch_df_r(const Op& op, const float4* x, const float4* u, float4* g_df, double* g64,
+                        int L, int block, cudaStream_t st) {
+  const unsigned grid = (unsigned)(((long long)op.g.V * (L / R) + block - 1) / block);
   const float2* links = reinterpret_cast<const float2*>(op.links32);
   if (g_df)
-    sweep_df_kernel<float4><<<grid, block, 0, st>>>(x, static_cast<float4*>(g_df), u, links,
-                                                    op.clov_inv32, op.g, L, (float)op.kappa,
-                                                    op.link12);
+    sweep_df_kernel<R, float4><<<grid, block, 0, st>>>(x, g_df, u, links, op.clov_inv32, op.g, L,
+                                                       (float)op.kappa, op.link12);
   else
-    sweep_df_kernel<double><<<grid, block, 0, st>>>(x, g64, u, links, op.clov_inv32, op.g, L,
-                                                    (float)op.kappa, op.link12);
+    sweep_df_kernel<R, double><<<grid, block, 0, st>>>(x, g64, u, links, op.clov_inv32, op.g, L,
+                                                       (float)op.kappa, op.link12);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_jacobi_df(const Op& op, const void* g_in, const void* u_df, void* g_df,
+                             double* g64, int L, int rhs_per_thread, int block, cudaStream_t st) {
+  if ((block != 64 && block != 128) || (rhs_per_thread != 1 && rhs_per_thread != 2) ||
+      L % rhs_per_thread != 0)
+    return cudaErrorInvalidValue;
+  const float4* x = static_cast<const float4*>(g_in);
+  const float4* u = static_cast<const float4*>(u_df);
+  float4* gd = static_cast<float4*>(g_df);
+  return rhs_per_thread == 2 ? launch_df_r<2>(op, x, u, gd, g64, L, block, st)
+                             : launch_df_r<1>(op, x, u, gd, g64, L, block, st);
 }

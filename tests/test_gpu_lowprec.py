@@ -232,3 +232,24 @@ def test_df_solve_near_critical_needs_no_fallback(wd):
     assert idf["iters"] <= i64["iters"] + 5
     assert S.true_residual(op, B, host(Xdf)).max() <= TRUE_RES_TOL
     assert rel(host(Xdf), host(X64)) <= SOLVE_X_TOL
+
+
+@pytest.mark.parametrize("tile", [(1, 128, 0, 0), (2, 128, 0, 0)])
+def test_df_sweep_tiles_match_oracle(wd, tile):
+    """Both double-float tiles (1 or 2 RHS per thread) compute the same sweep, and the autotuner
+    keeps one of them."""
+    dims, L, j = (3, 4, 5, 6), 6, 5
+    links = I.random_links(dims, 0.4, seed=2)
+    op = O.WilsonClover(links, dims, 0.12, 1.0)
+    R = I.gaussian_block(dims, L, seed=5)
+    ctx = wd.wd_create(dev(links), dims, 0.12, 1.0)
+    wd.wd_set_tile(ctx, L, *tile, precision=4)
+    G = host(wd.jacobi_precond(ctx, dev(R), j, precision=4))
+    assert wd.wd_tuned_tile(ctx, L, precision=4) == tile
+    assert rel(G, S.jacobi(op, R, j)) <= MIXED_TOL
+    ctx2 = wd.wd_create(dev(links), dims, 0.12, 1.0)
+    G2 = host(wd.jacobi_precond(ctx2, dev(R), j, precision=4))
+    assert wd.wd_tuned_tile(ctx2, L, precision=4) in ((1, 128, 0, 0), (2, 128, 0, 0))
+    assert rel(G2, G) <= 1e-13          # the two tiles differ only in the order of operations
+    with pytest.raises(wd.WDError):
+        wd.wd_set_tile(ctx, 3, 2, 128, precision=4)     # 2 does not divide L = 3
