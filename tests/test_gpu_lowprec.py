@@ -253,3 +253,23 @@ def test_df_sweep_tiles_match_oracle(wd, tile):
     assert rel(G2, G) <= 1e-13          # the two tiles differ only in the order of operations
     with pytest.raises(wd.WDError):
         wd.wd_set_tile(ctx, 3, 2, 128, precision=4)     # 2 does not divide L = 3
+
+
+@pytest.mark.parametrize("L", [1, 4, 12])
+@pytest.mark.parametrize("kappa", [0.125, 0.134])
+def test_df_dirs_form_across_L_and_kappa(wd, L, kappa):
+    """The default form (precision 5) on 8^3 x 16 for several L and kappa up to the bench's
+    near-critical value: oracle true residual <= 1e-12 per column, no fallback, and the FP64
+    form's solution to 1e-9."""
+    dims = (8, 8, 8, 16)
+    links = I.random_links(dims, 0.2, seed=0)
+    op = O.WilsonClover(links, dims, kappa, 1.0)
+    B = I.z4_noise(dims, L, seed=3)
+    ctx = wd.wd_create(dev(links), dims, kappa, 1.0)
+    X5, i5 = wd.bbicggr_solve(ctx, dev(B), j=12, tol=1e-12, precision=5)
+    X0, i0 = wd.bbicggr_solve(ctx, dev(B), j=12, tol=1e-12, precision=0)
+    assert i5["status"] == i0["status"] == wd.WD_OK
+    assert i5["fallbacks"] == 0
+    X5 = host(X5)
+    assert S.true_residual(op, B, X5).max() <= TRUE_RES_TOL
+    assert rel(X5, host(X0)) <= SOLVE_X_TOL
