@@ -239,7 +239,8 @@ const char* wd_profile_name(int kernel_class);
 
 /* Tile of the low-precision Jacobi sweep chosen by the autotuner for this L and storage
  * (precision 1: FP32 blocks, 3: BF16 blocks, 4: double-float sweeps, which take 1 or 2 RHS per
- * thread in 128-thread CTAs): RHS per thread, threads per CTA, the minimum
+ * thread in 128-thread CTAs, and staged 1 for the packed FP32x2 variant with 1 RHS per thread):
+ * RHS per thread, threads per CTA, the minimum
  * resident CTAs per SM the kernel was compiled for (0: none; 8: at most 128 registers a thread),
  * and whether each direction's neighbour data is staged in shared memory (cp.async, two stages)
  * while the previous direction is computed.  The autotuner times every candidate tile once, at

@@ -282,7 +282,8 @@ int autotune_lp(wd_ctx* c, int storage, int L, cudaStream_t s) {
 }
 
 // Double-float blocks take 16 bytes per complex number, like FP64 blocks.  The double-float sweep
-// takes 1 or 2 RHS per thread in 128-thread CTAs; the faster for this lattice and L is kept.
+// takes 1 or 2 RHS per thread in 128-thread CTAs, or 1 RHS in packed FP32x2 arithmetic; the
+// fastest for this lattice and L is kept.
 int ensure_workspace_df(wd_ctx* c, int L, cudaStream_t s) {
   const size_t bytes = (size_t)c->op.g.V * 12 * L * 16;
   for (auto& b : c->blk32) CHECK(b.ensure(bytes));
@@ -295,28 +296,30 @@ int ensure_workspace_df(wd_ctx* c, int L, cudaStream_t s) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
+  static const int cand[][2] = {{1, 0}, {2, 0}, {1, 1}};   // (RHS per thread, packed)
   float best = 1e30f;
-  int best_r = 1;
+  int best_i = 0;
   cudaError_t err = cudaSuccess;
-  for (int r = 1; r <= 2 && err == cudaSuccess; ++r) {
+  for (int i = 0; i < 3 && err == cudaSuccess; ++i) {
+    const int r = cand[i][0], pk = cand[i][1];
     if (L % r != 0) continue;
-    err = launch_jacobi_df(c->op, a, u_df, b, nullptr, L, r, 128, s);
+    err = launch_jacobi_df(c->op, a, u_df, b, nullptr, L, r, 128, pk, s);
     if (err == cudaSuccess) err = cudaEventRecord(e0, s);
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
-      err = launch_jacobi_df(c->op, a, u_df, b, nullptr, L, r, 128, s);
+      err = launch_jacobi_df(c->op, a, u_df, b, nullptr, L, r, 128, pk, s);
     if (err == cudaSuccess) err = cudaEventRecord(e1, s);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
     float ms = 0.f;
     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-    if (err == cudaSuccess && ms < best) { best = ms; best_r = r; }
+    if (err == cudaSuccess && ms < best) { best = ms; best_i = i; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CU(err);
-  c->tile_r[LP_DF][L] = best_r;
+  c->tile_r[LP_DF][L] = cand[best_i][0];
   c->tile_block[LP_DF][L] = 128;
   c->tile_minb[LP_DF][L] = 0;
-  c->tile_staged[LP_DF][L] = 0;
+  c->tile_staged[LP_DF][L] = cand[best_i][1];
   c->tile_set[LP_DF][L] = true;
   return WD_OK;
 }
@@ -376,7 +379,8 @@ int precondition(wd_ctx* c, const double* R, double* a, double* b, double** res,
       const bool last = i == j - 1;
       LAUNCH(WD_K_JACOBI_LP, 1,
              launch_jacobi_df(op, cur, u_df, last ? nullptr : nxt, last ? a : nullptr, L,
-                              c->tile_r[LP_DF][L], c->tile_block[LP_DF][L], s));
+                              c->tile_r[LP_DF][L], c->tile_block[LP_DF][L],
+                              c->tile_staged[LP_DF][L], s));
       if (hop_count) ++*hop_count;
       void* t = cur;
       cur = nxt;
@@ -696,9 +700,9 @@ int wd_set_tile(wd_ctx* c, int L, int precision, int rhs_per_thread, int block, 
   CHECK(check_L(L));
   int st;
   CHECK(tile_storage(precision, &st));
-  if (st == LP_DF) {   // 1 or 2 RHS per thread, 128 threads
+  if (st == LP_DF) {   // 1 or 2 RHS per thread, 128 threads; staged 1 = packed (1 RHS)
     if ((rhs_per_thread != 1 && rhs_per_thread != 2) || L % rhs_per_thread != 0 || block != 128 ||
-        min_blocks != 0 || staged != 0) {
+        min_blocks != 0 || (staged != 0 && staged != 1) || (staged == 1 && rhs_per_thread != 1)) {
       set_err("double-float tile (%d RHS/thread, %d threads) not available for L = %d",
               rhs_per_thread, block, L);
       return WD_EINVAL;
@@ -706,7 +710,7 @@ int wd_set_tile(wd_ctx* c, int L, int precision, int rhs_per_thread, int block, 
     c->tile_r[st][L] = rhs_per_thread;
     c->tile_block[st][L] = block;
     c->tile_minb[st][L] = 0;
-    c->tile_staged[st][L] = 0;
+    c->tile_staged[st][L] = staged;
     c->tile_set[st][L] = true;
     return WD_OK;
   }

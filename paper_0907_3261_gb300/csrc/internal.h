@@ -73,9 +73,11 @@ cudaError_t launch_jacobi_bf16_tiled(const Op& op, const void* g_in, const void*
 // blocks are component-major with one float4 (re.hi, re.lo, im.hi, im.lo) per complex number.
 cudaError_t launch_site_inverse_df(const Op& op, const double* u, void* u_df, void* g_df,
                                    double* g64, int L, cudaStream_t st);
-// One sweep with 1 or 2 RHS per thread (dividing L) and `block` (64 or 128) threads per CTA.
+// One sweep with 1 or 2 RHS per thread (dividing L) and `block` (64 or 128) threads per CTA;
+// packed 1 (with 1 RHS per thread) runs the FP32x2 (real, imaginary lanes) variant.
 cudaError_t launch_jacobi_df(const Op& op, const void* g_in, const void* u_df, void* g_df,
-                             double* g64, int L, int rhs_per_thread, int block, cudaStream_t st);
+                             double* g64, int L, int rhs_per_thread, int block, int packed,
+                             cudaStream_t st);
 
 // ---- clover.cu
 // Builds clov and clov_inv from links; *singular_dev receives 1 if some 6x6 block is singular.

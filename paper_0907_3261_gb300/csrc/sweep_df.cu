@@ -10,7 +10,7 @@
 // sums use Knuth's two-sum, so M is linear to ~1e-14.  On GB300, where FP64 runs at 1/61 of the
 // FP32 rate, this is several times faster than FP64 sweeps.
 //
-// Blocks are component-major, [spin*3+colour][site][rhs], one float4 (re.hi, re.lo, im.hi,
+// Blocks are component-major, [spin*3+colour][site][rhs], one float4 (re.hi, im.hi, re.lo,
 // im.lo) per complex number; one thread owns one site and 1 or 2 consecutive right-hand sides.  The first sweep converts the
 // FP64 right-hand side and stores its double-float copy; the last writes FP64 site-major.
 #include <type_traits>
@@ -64,13 +64,15 @@ WD_DEV void cmac(C& acc, Cx<float> a, C b) {
   dmac(acc.im, a.im, b.re);
 }
 
+// A stored element is (re.hi, im.hi, re.lo, im.lo): the two high words, then the two low words,
+// so that the packed kernel gets its (re, im) lane pairs straight from one 16-byte load.
 WD_DEV C ldq(const float4* p) {
   const float4 a = __ldg(p);
-  return {{a.x, a.y}, {a.z, a.w}};
+  return {{a.x, a.z}, {a.y, a.w}};
 }
 WD_DEV void stq(float4* p, C z) {
   const DF re = df_norm(z.re), im = df_norm(z.im);
-  *p = make_float4(re.hi, re.lo, im.hi, im.lo);
+  *p = make_float4(re.hi, im.hi, re.lo, im.lo);
 }
 WD_DEV void stq(double* p, C z) { stc(p, cdf_to(z)); }
 
@@ -287,6 +289,190 @@ sweep_df_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4* 
   }
 }
 
+// ------------------------------------------------------------------ packed variant
+// The same sweep with the real and imaginary halves of every double-float value in the two lanes
+// of FP32x2 instructions (FFMA2/FADD2/FMUL2, each lane an IEEE round-to-nearest operation), which
+// halves the instructions the scheduler issues.  A value is hi = (re.hi, im.hi), lo = (re.lo,
+// im.lo).  Subtractions are FMAs with a (-1, -1) operand (negation is exact).  A complex product
+// sum  sum_b a_b h_b  is accumulated as X = sum ar_b (h_b.re, h_b.im) and Y = sum ai_b (h_b.re,
+// h_b.im) with broadcast operator lanes, and combined once: (re, im) = X + (-Y.im, Y.re).
+struct P2 {
+  float2 hi, lo;
+};
+WD_DEV float2 dup(float a) { return make_float2(a, a); }
+WD_DEV P2 pzero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+WD_DEV P2 pswap(P2 z) { return {make_float2(z.hi.y, z.hi.x), make_float2(z.lo.y, z.lo.x)}; }
+WD_DEV P2 psel(bool c, P2 a, P2 b) { return c ? a : b; }
+
+// s + e = a + sg b exactly in each lane (sg = +1 or -1 per lane); two-sum with the sign folded in.
+WD_DEV void two_sum2(float2 a, float2 b, float2 sg, float2 m1, float2& s, float2& e) {
+  s = __ffma2_rn(sg, b, a);
+  const float2 nbb = __ffma2_rn(s, m1, a);   // a - s: minus the part of sg b that reached s
+  const float2 t1 = __fadd2_rn(s, nbb);      // s - bb
+  const float2 t2 = __ffma2_rn(t1, m1, a);   // a - (s - bb)
+  const float2 t3 = __ffma2_rn(sg, b, nbb);  // sg b - bb
+  e = __fadd2_rn(t2, t3);
+}
+WD_DEV P2 padd(P2 a, P2 b, float2 sg, float2 m1) {   // a + sg b
+  float2 s, e;
+  two_sum2(a.hi, b.hi, sg, m1, s, e);
+  return {s, __fadd2_rn(__ffma2_rn(sg, b.lo, a.lo), e)};
+}
+// acc + a b for an FP32 operator value a broadcast to both lanes (na = -a).
+WD_DEV void pmac(P2& acc, float2 a, float2 na, P2 b, float2 m1) {
+  const float2 np = __fmul2_rn(na, b.hi);   // -(a b.hi), rounded
+  float2 e = __ffma2_rn(a, b.hi, np);       // the rounding error of a b.hi, exactly
+  e = __ffma2_rn(a, b.lo, e);
+  float2 s, t;
+  two_sum2(acc.hi, np, m1, m1, s, t);       // acc.hi - np
+  acc.hi = s;
+  acc.lo = __fadd2_rn(acc.lo, __fadd2_rn(t, e));
+}
+WD_DEV P2 pmul(float2 a, float2 na, P2 b) {   // a b as the first term of a sum
+  const float2 p = __fmul2_rn(a, b.hi);
+  const float2 np = __fmul2_rn(na, b.hi);
+  const float2 e = __ffma2_rn(a, b.hi, np);
+  return {p, __ffma2_rn(a, b.lo, e)};
+}
+// (re, im) = X + (-Y.im, Y.re): the complex product sum from its two broadcast accumulators.
+WD_DEV P2 pcombine(P2 X, P2 Y, float2 m1) { return padd(X, pswap(Y), make_float2(-1.f, 1.f), m1); }
+
+WD_DEV P2 ldq2(const float4* p) {
+  const float4 a = __ldg(p);
+  return {make_float2(a.x, a.y), make_float2(a.z, a.w)};
+}
+WD_DEV void stq2(float4* p, P2 z, float2 m1) {   // renormalise both lanes, then store
+  const float2 s = __fadd2_rn(z.hi, z.lo);
+  const float2 lo = __ffma2_rn(__ffma2_rn(z.hi, m1, s), m1, z.lo);   // lo - (s - hi)
+  *p = make_float4(s.x, s.y, lo.x, lo.y);
+}
+WD_DEV void stq2(double* p, P2 z, float2) {
+  stc(p, cmake<double>((double)z.hi.x + (double)z.lo.x, (double)z.hi.y + (double)z.lo.y));
+}
+
+// The hopping term H x at (s, r) in packed arithmetic (one rolled, branch-free loop body as in
+// hopping<R>).
+WD_DEV void hopping2(const float4* __restrict__ x, const float2* __restrict__ links, const Geom& g,
+                     int s, const int c[4], int r, int L, bool link12, P2 au[2][3], P2 ad[2][3],
+                     float2 m1) {
+  const size_t V = (size_t)g.V;
+  const size_t cs = V * L;
+  const float2 one = make_float2(1.f, 1.f);
+#pragma unroll 1
+  for (int d = 0; d < 8; ++d) {
+    const int mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    const int cm = mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
+    const int ext = g.d[mu], str = g.stride[mu];
+    const int sn = fwd ? (cm == ext - 1 ? s - (ext - 1) * str : s + str)
+                       : (cm == 0 ? s + (ext - 1) * str : s - str);
+    const SpinDir sd = spin_dir(d);
+    const float2 dn0 = make_float2(sd.dn[0], sd.dn[1]), dn1 = make_float2(sd.dn[2], sd.dn[3]);
+    const float2 up0 = make_float2(sd.up[0], sd.up[1]), up1 = make_float2(sd.up[2], sd.up[3]);
+    const float4* base = x + (size_t)sn * L + r;
+    const int k0 = sd.cross ? 9 : 6, k1 = sd.cross ? 6 : 9;
+    P2 h0[3], h1[3];
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const P2 u0 = ldq2(base + (0 * 3 + col) * cs), u1 = ldq2(base + (1 * 3 + col) * cs);
+      const P2 x0 = ldq2(base + (k0 + col) * cs), x1 = ldq2(base + (k1 + col) * cs);
+      h0[col] = padd(u0, psel(sd.swap, pswap(x0), x0), dn0, m1);
+      h1[col] = padd(u1, psel(sd.swap, pswap(x1), x1), dn1, m1);
+    }
+    Cx<float> m[3][3];
+    link(links + (size_t)mu * 9 * V + (fwd ? s : sn), V, link12, m);
+    if (!fwd) {   // W = m^H
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 3; ++b) {
+          const Cx<float> t = m[a][b];
+          m[a][b] = conj(m[b][a]);
+          m[b][a] = conj(t);
+        }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) m[a][a] = conj(m[a][a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float2 r0 = dup(m[a][0].re), nr0 = dup(-m[a][0].re);
+      const float2 i0 = dup(m[a][0].im), ni0 = dup(-m[a][0].im);
+      P2 X0 = pmul(r0, nr0, h0[0]), Y0 = pmul(i0, ni0, h0[0]);
+      P2 X1 = pmul(r0, nr0, h1[0]), Y1 = pmul(i0, ni0, h1[0]);
+#pragma unroll
+      for (int b = 1; b < 3; ++b) {
+        const float2 rb = dup(m[a][b].re), nrb = dup(-m[a][b].re);
+        const float2 ib = dup(m[a][b].im), nib = dup(-m[a][b].im);
+        pmac(X0, rb, nrb, h0[b], m1);
+        pmac(Y0, ib, nib, h0[b], m1);
+        pmac(X1, rb, nrb, h1[b], m1);
+        pmac(Y1, ib, nib, h1[b], m1);
+      }
+      const P2 w0 = pcombine(X0, Y0, m1), w1 = pcombine(X1, Y1, m1);
+      au[0][a] = padd(au[0][a], w0, one, m1);
+      au[1][a] = padd(au[1][a], w1, one, m1);
+      const P2 y0 = psel(sd.cross, w1, w0), y1 = psel(sd.cross, w0, w1);
+      ad[0][a] = padd(ad[0][a], psel(sd.swap, pswap(y0), y0), up0, m1);
+      ad[1][a] = padd(ad[1][a], psel(sd.swap, pswap(y1), y1), up1, m1);
+    }
+  }
+}
+
+// Row i of a packed Hermitian 6x6 FP32 block times v (as herm6_row), in packed arithmetic.
+WD_DEV P2 herm6_row2(const float* __restrict__ m, size_t stride, int i, const P2 v[6], float2 m1) {
+  P2 X, Y;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int t = c_h6_off[i][j];
+    const float sg = c_h6_sgn[i][j];
+    const float re = __ldg(m + t * stride);
+    const float im = sg * __ldg(m + (t + (sg != 0.f)) * stride);
+    if (j == 0) {
+      X = pmul(dup(re), dup(-re), v[0]);
+      Y = pmul(dup(im), dup(-im), v[0]);
+    } else {
+      pmac(X, dup(re), dup(-re), v[j], m1);
+      pmac(Y, dup(im), dup(-im), v[j], m1);
+    }
+  }
+  return pcombine(X, Y, m1);
+}
+
+template <typename TY>
+__global__ void __launch_bounds__(128, 4)
+sweep_df2_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4* __restrict__ u,
+                 const float2* __restrict__ links, const float* __restrict__ clov_inv, Geom g,
+                 int L, float kappa, int link12) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= g.V * L) return;
+  const int s = tid / L;
+  const int r = tid - s * L;
+  const size_t V = (size_t)g.V;
+  const float2 m1 = make_float2(-1.f, -1.f);
+  int c[4];
+  site_coords(g, s, c);
+  P2 au[2][3], ad[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) { au[a][b] = pzero(); ad[a][b] = pzero(); }
+  hopping2(x, links, g, s, c, r, L, link12 != 0, au, ad, m1);
+  const float2 kap = dup(kappa), nkap = dup(-kappa);
+#pragma unroll 1
+  for (int ch = 0; ch < 2; ++ch) {
+    P2 vin[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const int k = ch * 6 + i;
+      vin[i] = ldq2(u + ((size_t)k * V + s) * L + r);
+      pmac(vin[i], kap, nkap, ch == 0 ? au[i / 3][i % 3] : ad[i / 3][i % 3], m1);
+    }
+    const float* mm = clov_inv + (size_t)ch * CLOV_REALS * V + s;
+#pragma unroll 1
+    for (int i = 0; i < 6; ++i) stq2(at(y, V, L, s, ch * 6 + i, r), herm6_row2(mm, V, i, vin, m1), m1);
+  }
+}
+
 // First sweep from G = 0: stores the double-float copy of the FP64 right-hand side (when u_df is
 // not null) and writes G = A_D^{-1} U.
 template <typename TY>
@@ -348,13 +534,25 @@ cudaError_t launch_df_r(const Op& op, const float4* x, const float4* u, float4* 
 }  // namespace
 
 cudaError_t launch_jacobi_df(const Op& op, const void* g_in, const void* u_df, void* g_df,
-                             double* g64, int L, int rhs_per_thread, int block, cudaStream_t st) {
+                             double* g64, int L, int rhs_per_thread, int block, int packed,
+                             cudaStream_t st) {
   if ((block != 64 && block != 128) || (rhs_per_thread != 1 && rhs_per_thread != 2) ||
-      L % rhs_per_thread != 0)
+      L % rhs_per_thread != 0 || (packed && rhs_per_thread != 1))
     return cudaErrorInvalidValue;
   const float4* x = static_cast<const float4*>(g_in);
   const float4* u = static_cast<const float4*>(u_df);
   float4* gd = static_cast<float4*>(g_df);
+  if (packed) {
+    const unsigned grid = (unsigned)(((long long)op.g.V * L + block - 1) / block);
+    const float2* links = reinterpret_cast<const float2*>(op.links32);
+    if (gd)
+      sweep_df2_kernel<float4><<<grid, block, 0, st>>>(x, gd, u, links, op.clov_inv32, op.g, L,
+                                                       (float)op.kappa, op.link12);
+    else
+      sweep_df2_kernel<double><<<grid, block, 0, st>>>(x, g64, u, links, op.clov_inv32, op.g, L,
+                                                       (float)op.kappa, op.link12);
+    return cudaGetLastError();
+  }
   return rhs_per_thread == 2 ? launch_df_r<2>(op, x, u, gd, g64, L, block, st)
                              : launch_df_r<1>(op, x, u, gd, g64, L, block, st);
 }

@@ -189,13 +189,16 @@ def nonlinearity(wd, ctx, x, y, j, precision):
 
 @pytest.mark.parametrize("dims,L,j", [((4, 4, 4, 8), 6, 12), ((16, 16, 16, 32), 12, 12)])
 def test_df_preconditioner_is_linear(wd, dims, L, j):
-    """Double-float M is linear to ~1e-13 at any size, FP32 M only to ~1e-7 -- the property
-    block BiCGGR relies on (the test also shows that it tells the two apart)."""
+    """Double-float M is linear to ~1e-13 at any size, in every double-float tile, FP32 M only
+    to ~1e-7 -- the property block BiCGGR relies on (the test also shows that it tells the two
+    apart)."""
     links = I.random_links(dims, 0.2, seed=0)
     ctx = wd.wd_create(dev(links), dims, 0.134, 1.0)
     x = I.z4_noise(dims, L, seed=3)
     y = I.gaussian_block(dims, L, seed=4)
-    assert nonlinearity(wd, ctx, x, y, j, 4) <= DF_LINEARITY_TOL
+    for tile in ((1, 128, 0, 0), (1, 128, 0, 1)):
+        wd.wd_set_tile(ctx, L, *tile, precision=4)
+        assert nonlinearity(wd, ctx, x, y, j, 4) <= DF_LINEARITY_TOL
     assert nonlinearity(wd, ctx, x, y, j, 1) > 100 * DF_LINEARITY_TOL
 
 
@@ -234,7 +237,7 @@ def test_df_solve_near_critical_needs_no_fallback(wd):
     assert rel(host(Xdf), host(X64)) <= SOLVE_X_TOL
 
 
-@pytest.mark.parametrize("tile", [(1, 128, 0, 0), (2, 128, 0, 0)])
+@pytest.mark.parametrize("tile", [(1, 128, 0, 0), (2, 128, 0, 0), (1, 128, 0, 1)])
 def test_df_sweep_tiles_match_oracle(wd, tile):
     """Both double-float tiles (1 or 2 RHS per thread) compute the same sweep, and the autotuner
     keeps one of them."""
@@ -249,10 +252,12 @@ def test_df_sweep_tiles_match_oracle(wd, tile):
     assert rel(G, S.jacobi(op, R, j)) <= MIXED_TOL
     ctx2 = wd.wd_create(dev(links), dims, 0.12, 1.0)
     G2 = host(wd.jacobi_precond(ctx2, dev(R), j, precision=4))
-    assert wd.wd_tuned_tile(ctx2, L, precision=4) in ((1, 128, 0, 0), (2, 128, 0, 0))
-    assert rel(G2, G) <= 1e-13          # the two tiles differ only in the order of operations
+    assert wd.wd_tuned_tile(ctx2, L, precision=4) in ((1, 128, 0, 0), (2, 128, 0, 0), (1, 128, 0, 1))
+    assert rel(G2, G) <= 1e-13          # the tiles differ only in the order of operations
     with pytest.raises(wd.WDError):
         wd.wd_set_tile(ctx, 3, 2, 128, precision=4)     # 2 does not divide L = 3
+    with pytest.raises(wd.WDError):
+        wd.wd_set_tile(ctx, 4, 2, 128, 0, 1, precision=4)   # the packed variant takes 1 RHS
 
 
 @pytest.mark.parametrize("L", [1, 4, 12])
