@@ -50,16 +50,16 @@ FORM_NAMES = {"fp64": "plain FP64 Jacobi", "mixed": "mixed: FP32 Jacobi precondi
               "bf16": "mixed: Jacobi preconditioner on BF16-stored blocks",
               "df": "mixed: double-float Jacobi preconditioner (FP32 pairs, FP32 operator)",
               "df_dirs": "mixed: double-float preconditioner and direction recurrences"}
-# FP32 instructions per site and RHS of one double-float sweep, counting a split product (FP32
-# operator entry x FP32-pair value, added into a sum with two-sum) as 11, the first product of a sum
-# as 3 and a two-sum addition as 8.  Each of the 8 hops: 12 additions for the projection, the link
+# FP32 lane operations (a packed FP32x2 instruction is two) per site and RHS of one double-float
+# sweep, counting a split product (FP32 operator entry x FP32-pair value, added into a sum with
+# two-sum) as 11, the first product of a sum as 3 and a two-sum addition as 8.  Each of the 8 hops: 12 additions for the projection, the link
 # times two half-spinors (6 sums of 3 complex products: 6 x (2 x 3 + 2 x 11) + 12 x 4 x 11) and 24
 # additions into the sums; the row-2 rebuild of the 8 links (30 each); the two 6x6 blocks (12 rows
 # of 1 real and 5 complex products: 6 + 5 x 44 or 28 + 4 x 44 + 22 = 226); U + kappa H (24 split
 # products) and normalising the 24 stored reals (3 each).
 DF_OPS = 8 * (12 * 8 + 6 * (2 * 3 + 2 * 11) + 12 * 4 * 11 + 24 * 8) + 8 * 30 + 12 * 226 \
     + 24 * 11 + 24 * 3
-FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12   # FP32 lane instructions per second (2070 MHz)
+FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12   # FP32 lane operations per second (2070 MHz)
 METRIC = "time-to-solution at true resid 1e-12 for L RHS; Dslash HBM GB/s vs peak"
 FLOP_APPLY = 1824          # flop per site per RHS of A (1320 hopping + 504 clover)
 FLOP_JACOBI = 1872         # flop per site per RHS of one Jacobi sweep A_D^{-1}(U + kappa H G)
@@ -500,7 +500,7 @@ def main():
         if kprec == "df":
             tops = DF_OPS * V * L_RHS / avg_s / 1e12
             fig = {"bound": "alu", "achieved": round(tops, 3), "peak": round(FP32_PEAK_TOPS, 2),
-                   "unit": "T FP32 instructions/s", "frac": round(tops / FP32_PEAK_TOPS, 4),
+                   "unit": "T FP32 lane ops/s", "frac": round(tops / FP32_PEAK_TOPS, 4),
                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
                    "fp32_ops_per_site_rhs": DF_OPS, "tflops_fp64_equivalent": round(tflops, 3),
                    "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
