@@ -382,10 +382,12 @@ update_pv_kernel(double* __restrict__ P, double* __restrict__ V, const double* _
 // updates and the column norms stay FP64: X and R are updated with the F, G whose products with A
 // are subtracted from R, so R = B - AX holds to FP64 rounding whatever precision the directions
 // U, P, V and the coefficients alpha, gamma are computed in.
-WD_DEV CDF ldcdf(const double* p, size_t e) { return cdf_from(ld2(p, e)); }
+// Block elements convert through the bit-field forms (no FP64 pipe); the L x L coefficients,
+// a few hundred per launch, through the rounding conversions.
+WD_DEV CDF ldcdf(const double* p, size_t e) { return cdf_split(ld2(p, e)); }
 WD_DEV CDF cdf_of(double2 v) { return cdf_from(Cx<double>{v.x, v.y}); }
 WD_DEV double2 d2_of(CDF z) {
-  const Cx<double> c = cdf_to({df_norm(z.re), df_norm(z.im)});
+  const Cx<double> c = cdf_join({df_norm(z.re), df_norm(z.im)});
   return make_double2(c.re, c.im);
 }
 
@@ -457,7 +459,7 @@ update_xr_df_kernel(double* __restrict__ X, const double* __restrict__ F, const 
       const Cx<double> r = ld2(R, q) - cmul(z, ld2(W, q)) - ld2(Y, q);
       st2(X, q, x);
       st2(R, q, r);
-      Bs[e] = cdf_from(r);
+      Bs[e] = cdf_split(r);
       As[e] = ldcdf(Rt, q);
       nred[e] = cnorm2(r);
     }
@@ -509,7 +511,7 @@ update_pv_df_kernel(double* __restrict__ P, double* __restrict__ V, const double
       const Cx<double> v = ld2(W, q) + Cx<double>{yd.x, yd.y};
       st2(P, q, pv);
       st2(V, q, v);
-      Vs[e] = cdf_from(v);
+      Vs[e] = cdf_split(v);
     }
     __syncthreads();
     gram_chunk_df(Rs, Vs, nr, L, acc);

@@ -106,6 +106,47 @@ WD_DEV DF df_from(double d) {
   return {hi, __double2float_rn(d - (double)hi)};
 }
 WD_DEV double df_to(DF a) { return (double)a.hi + (double)a.lo; }
+// The same two conversions built from the IEEE-754 bit fields on the integer and FP32 pipes.  On
+// GB300 the FP64 pipe issues two lanes per clock per SM, and the FP64 <-> FP32 conversions above
+// run on it; the bulk conversions of whole blocks use these instead.
+//   df_split: hi = d truncated to 24 significant bits; lo = d - hi rounded to nearest FP32.  The
+//   remainder (29 fraction bits r) enters as two exact differences 2^E (1 + f) - 2^E, one for the
+//   top 23 bits of r and one for its low 6, and their FP32 sum rounds once, so
+//   |d - (hi + lo)| <= 2^-48 |d| for |d| >= 2^-79.  Below that lo keeps fewer bits, below 2^-103
+//   none, and below 2^-126 hi is 0.  Values beyond the FP32 range become +-inf; NaN stays NaN.
+WD_DEV DF df_split(double d) {
+  const unsigned int h = (unsigned int)__double2hiint(d), l = (unsigned int)__double2loint(d);
+  const unsigned int s = h & 0x80000000u;
+  const int e = (int)((h >> 20) & 0x7FFu);                    // biased FP64 exponent
+  const unsigned int m = __funnelshift_l(l, h, 3) & 0x7FFFFFu;  // top 23 fraction bits
+  const unsigned int r = l & 0x1FFFFFFFu;                      // the other 29
+  unsigned int hb = s | ((unsigned int)(e - 896) << 23) | m;
+  const unsigned int b1 = s | ((unsigned int)(e - 919) << 23);   // 2^(e-1046): r >> 6 in units of 2^(e-1069)
+  const unsigned int b2 = s | ((unsigned int)(e - 942) << 23);   // 2^(e-1069): r & 63 in units of 2^(e-1075)
+  const float t1 = __fsub_rn(__uint_as_float(b1 | (r >> 6)), __uint_as_float(b1));
+  const float t2 = __fsub_rn(__uint_as_float(b2 | ((r & 63u) << 17)), __uint_as_float(b2));
+  float lo = __fadd_rn(t1, t2);
+  if (e < 943) lo = e < 920 ? 0.f : t1;
+  if (e < 897) hb = s;
+  if (e > 1150) {
+    hb = (e == 2047 && ((h & 0xFFFFFu) | l)) ? 0x7FC00000u : (s | 0x7F800000u);
+    lo = 0.f;
+  }
+  return {__uint_as_float(hb), lo};
+}
+//   f_widen: the FP64 value of an FP32 number, exact for normal numbers, 0 for FP32 subnormals.
+WD_DEV double f_widen(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int e = (b >> 23) & 0xFFu;
+  unsigned int hw = (b & 0x80000000u) | ((e == 255u ? 2047u : e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  unsigned int lw = b << 29;
+  if (e == 0u) {
+    hw = b & 0x80000000u;
+    lw = 0u;
+  }
+  return __hiloint2double((int)hw, (int)lw);
+}
+WD_DEV double df_join(DF a) { return f_widen(a.hi) + f_widen(a.lo); }
 // s + e = a + b exactly.  The __f*_rn intrinsics are never contracted into FMAs, which would
 // break the exactness the transformation relies on.
 WD_DEV void two_sum(float a, float b, float& s, float& e) {
@@ -136,6 +177,8 @@ struct CDF {
 };
 WD_DEV CDF cdf_from(Cx<double> z) { return {df_from(z.re), df_from(z.im)}; }
 WD_DEV Cx<double> cdf_to(CDF z) { return {df_to(z.re), df_to(z.im)}; }
+WD_DEV CDF cdf_split(Cx<double> z) { return {df_split(z.re), df_split(z.im)}; }
+WD_DEV Cx<double> cdf_join(CDF z) { return {df_join(z.re), df_join(z.im)}; }
 WD_DEV CDF cdf_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
 // acc += a * b (complex)
 WD_DEV void cdf_mac(CDF& acc, CDF a, CDF b) {

@@ -74,7 +74,7 @@ WD_DEV void stq(float4* p, C z) {
   const DF re = df_norm(z.re), im = df_norm(z.im);
   *p = make_float4(re.hi, im.hi, re.lo, im.lo);
 }
-WD_DEV void stq(double* p, C z) { stc(p, cdf_to(z)); }
+WD_DEV void stq(double* p, C z) { stc(p, cdf_join(z)); }
 
 // Address of component k of (site s, rhs r): component-major element, or site-major FP64.
 template <typename TY>
@@ -347,7 +347,7 @@ WD_DEV void stq2(float4* p, P2 z, float2 m1) {   // renormalise both lanes, then
   *p = make_float4(s.x, s.y, lo.x, lo.y);
 }
 WD_DEV void stq2(double* p, P2 z, float2) {
-  stc(p, cmake<double>((double)z.hi.x + (double)z.lo.x, (double)z.hi.y + (double)z.lo.y));
+  stc(p, cmake<double>(f_widen(z.hi.x) + f_widen(z.lo.x), f_widen(z.hi.y) + f_widen(z.lo.y)));
 }
 
 // The hopping term H x at (s, r) in packed arithmetic (one rolled, branch-free loop body as in
@@ -490,7 +490,7 @@ site_inverse_df_kernel(const double* __restrict__ u, float4* __restrict__ u_df, 
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       const int k = ch * 6 + i;
-      vin[0][i] = cdf_from(ldc(u + base + 2 * (size_t)(k * L)));
+      vin[0][i] = cdf_split(ldc(u + base + 2 * (size_t)(k * L)));
       if (u_df) stq(at(u_df, (size_t)V, L, s, k, r), vin[0][i]);
     }
     const float* m = clov_inv + (size_t)ch * CLOV_REALS * V + s;
