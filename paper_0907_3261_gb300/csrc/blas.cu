@@ -378,26 +378,33 @@ update_pv_kernel(double* __restrict__ P, double* __restrict__ V, const double* _
 
 // ---------------------------------------------------------------- double-float variants
 // The same three updates with every product of an N x L block by an L x L matrix, and the Gram
-// products, in double-float arithmetic (FP32 pairs, ~48 bits) on the FP32 pipes.  The X and R
-// updates and the column norms stay FP64: X and R are updated with the F, G whose products with A
-// are subtracted from R, so R = B - AX holds to FP64 rounding whatever precision the directions
-// U, P, V and the coefficients alpha, gamma are computed in.
-// Block elements convert through the bit-field forms (no FP64 pipe); the L x L coefficients,
-// a few hundred per launch, through the rounding conversions.
-WD_DEV CDF ldcdf(const double* p, size_t e) { return cdf_split(ld2(p, e)); }
+// products, in double-float arithmetic (FP32 pairs, ~48 bits) on the FP32 pipes, packed two lanes
+// per instruction: the (re, im) halves of a block element share one FP32x2 value, and the factor
+// from the L x L matrix (or the other Gram operand) enters both lanes.  The X and R updates and the
+// column norms stay FP64: X and R are updated with the F, G whose products with A are subtracted
+// from R, so R = B - AX holds to FP64 rounding whatever precision the directions U, P, V and the
+// coefficients alpha, gamma are computed in.  Block elements convert through the bit-field forms
+// (no FP64 pipe); the L x L coefficients, a few hundred per launch, through the rounding ones.
 WD_DEV CDF cdf_of(double2 v) { return cdf_from(Cx<double>{v.x, v.y}); }
-WD_DEV double2 d2_of(CDF z) {
-  const Cx<double> c = cdf_join({df_norm(z.re), df_norm(z.im)});
-  return make_double2(c.re, c.im);
+WD_DEV P2 ldp2(const double* p, size_t e) { return p2_split(reinterpret_cast<const double2*>(p)[e]); }
+// acc + g b for a double-float complex coefficient g: X and Y of the product sum (see pcombine).
+WD_DEV void pmac_coef(P2& X, P2& Y, const CDF& g, P2 b, float2 m1) {
+  pmac_dd(X, dup(g.re.hi), dup(-g.re.hi), dup(g.re.lo), b, m1);
+  pmac_dd(Y, dup(g.im.hi), dup(-g.im.hi), dup(g.im.lo), b, m1);
 }
 
 __global__ void __launch_bounds__(TS_THREADS)
 update_u_df_kernel(const double* __restrict__ P, const double* __restrict__ V, double* __restrict__ U,
                    int L, long long rows, const SolverState* __restrict__ st) {
-  __shared__ CDF Ss[CHE];
+  __shared__ P2 Ss[CHE];
   __shared__ CDF al[WD_LMAX * WD_LMAX];
   if (st->status != ST_OK) return;
+  const float2 m1 = make_float2(-1.f, -1.f);
   const CDF z = cdf_of(st->zeta);
+  // -zeta v = (-z.re) (v.re, v.im) + (z.im, -z.im) (v.im, v.re)
+  const float2 a1 = dup(-z.re.hi), na1 = dup(z.re.hi), a1lo = dup(-z.re.lo);
+  const float2 a2 = make_float2(z.im.hi, -z.im.hi), na2 = make_float2(-z.im.hi, z.im.hi);
+  const float2 a2lo = make_float2(z.im.lo, -z.im.lo);
   for (int e = threadIdx.x; e < L * L; e += blockDim.x) al[e] = cdf_of(st->alpha[e]);
   const long long nchunks = (rows + CH - 1) / CH;
   for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
@@ -407,31 +414,36 @@ update_u_df_kernel(const double* __restrict__ P, const double* __restrict__ V, d
     const size_t e0 = (size_t)r0 * L;
     __syncthreads();
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      CDF sv = ldcdf(P, e0 + e);
-      const CDF v = ldcdf(V, e0 + e);
-      cdf_mac(sv, {{-z.re.hi, -z.re.lo}, {-z.im.hi, -z.im.lo}}, v);   // P - zeta V
+      P2 sv = ldp2(P, e0 + e);
+      const P2 v = ldp2(V, e0 + e);
+      pmac_dd(sv, a1, na1, a1lo, v, m1);          // P - zeta V
+      pmac_dd(sv, a2, na2, a2lo, pswap(v), m1);
       Ss[e] = sv;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
       const int n = e / L, b = e - (e / L) * L;
-      CDF acc = cdf_zero();
-      for (int a = 0; a < L; ++a) cdf_mac(acc, Ss[n * L + a], al[a * L + b]);
-      reinterpret_cast<double2*>(U)[e0 + e] = d2_of(acc);
+      P2 X = pzero(), Y = pzero();
+      for (int a = 0; a < L; ++a) pmac_coef(X, Y, al[a * L + b], Ss[n * L + a], m1);
+      reinterpret_cast<double2*>(U)[e0 + e] = p2_join(pcombine(X, Y, m1));
     }
   }
 }
 
-// Long sums (thousands of rows per block): the accumulator is renormalised after every product,
-// so its low word never outgrows ulp(hi) and keeps ~48-bit accuracy.
-WD_DEV void gram_chunk_df(const CDF* As, const CDF* Bs, int rows, int L, CDF& acc) {
+// Gram entry (a, b) of a chunk: sum_n conj(A[n, a]) B[n, b] into X, Y (see pcombine_conj).  Long
+// sums (thousands of rows per block): both accumulators are renormalised after every product, so
+// their low words never outgrow ulp(hi) and keep ~48-bit accuracy.
+WD_DEV void gram_chunk_p2(const P2* As, const P2* Bs, int rows, int L, P2& X, P2& Y, float2 m1) {
   const int t = threadIdx.x;
   if (t < L * L) {
     const int a = t / L, b = t - (t / L) * L;
     for (int n = 0; n < rows; ++n) {
-      cdf_macj(acc, As[n * L + a], Bs[n * L + b]);
-      acc.re = df_norm(acc.re);
-      acc.im = df_norm(acc.im);
+      const P2 x = As[n * L + a];
+      const P2 y = Bs[n * L + b];
+      pmac_dd(X, dup(x.hi.x), dup(-x.hi.x), dup(x.lo.x), y, m1);
+      pmac_dd(Y, dup(x.hi.y), dup(-x.hi.y), dup(x.lo.y), y, m1);
+      X = pnorm(X, m1);
+      Y = pnorm(Y, m1);
     }
   }
 }
@@ -441,11 +453,12 @@ update_xr_df_kernel(double* __restrict__ X, const double* __restrict__ F, const 
                     double* __restrict__ R, const double* __restrict__ W, const double* __restrict__ Y,
                     const double* __restrict__ Rt, int L, long long rows, double2* __restrict__ part,
                     const SolverState* __restrict__ st) {
-  __shared__ CDF As[CHE], Bs[CHE];
+  __shared__ P2 As[CHE], Bs[CHE];
   __shared__ double nred[CHE];
   if (st->status != ST_OK) return;
+  const float2 m1 = make_float2(-1.f, -1.f);
   const Cx<double> z = sm(st->zeta);
-  CDF acc = cdf_zero();
+  P2 gx = pzero(), gy = pzero();
   double nacc = 0.0;
   const long long nchunks = (rows + CH - 1) / CH;
   for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
@@ -459,18 +472,18 @@ update_xr_df_kernel(double* __restrict__ X, const double* __restrict__ F, const 
       const Cx<double> r = ld2(R, q) - cmul(z, ld2(W, q)) - ld2(Y, q);
       st2(X, q, x);
       st2(R, q, r);
-      Bs[e] = cdf_split(r);
-      As[e] = ldcdf(Rt, q);
+      Bs[e] = p2_split(make_double2(r.re, r.im));
+      As[e] = ldp2(Rt, q);
       nred[e] = cnorm2(r);
     }
     __syncthreads();
-    gram_chunk_df(As, Bs, nr, L, acc);
+    gram_chunk_p2(As, Bs, nr, L, gx, gy, m1);
     if (threadIdx.x < L)
       for (int n = 0; n < nr; ++n) nacc += nred[n * L + threadIdx.x];
     __syncthreads();
   }
   double2* p = part + (size_t)blockIdx.x * PART_STRIDE;
-  if (threadIdx.x < L * L) p[threadIdx.x] = d2_of(acc);
+  if (threadIdx.x < L * L) p[threadIdx.x] = p2_join(pcombine_conj(gx, gy, m1));
   if (threadIdx.x < L) p[WD_LMAX * WD_LMAX + threadIdx.x] = make_double2(nacc, 0.0);
 }
 
@@ -479,11 +492,12 @@ update_pv_df_kernel(double* __restrict__ P, double* __restrict__ V, const double
                     const double* __restrict__ W, const double* __restrict__ U,
                     const double* __restrict__ Y, const double* __restrict__ Rt, int L,
                     long long rows, double2* __restrict__ part, const SolverState* __restrict__ st) {
-  __shared__ CDF Us[CHE], Ys[CHE], Vs[CHE], Rs[CHE];
+  __shared__ P2 Us[CHE], Ys[CHE], Vs[CHE], Rs[CHE];
   __shared__ CDF ga[WD_LMAX * WD_LMAX];
   if (st->status != ST_OK) return;
+  const float2 m1 = make_float2(-1.f, -1.f);
   for (int e = threadIdx.x; e < L * L; e += blockDim.x) ga[e] = cdf_of(st->gamma[e]);
-  CDF acc = cdf_zero();
+  P2 gx = pzero(), gy = pzero();
   const long long nchunks = (rows + CH - 1) / CH;
   for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
     const long long r0 = ck * CH;
@@ -492,32 +506,32 @@ update_pv_df_kernel(double* __restrict__ P, double* __restrict__ V, const double
     const size_t e0 = (size_t)r0 * L;
     __syncthreads();
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      Us[e] = ldcdf(U, e0 + e);
-      Ys[e] = ldcdf(Y, e0 + e);
-      Rs[e] = ldcdf(Rt, e0 + e);
+      Us[e] = ldp2(U, e0 + e);
+      Ys[e] = ldp2(Y, e0 + e);
+      Rs[e] = ldp2(Rt, e0 + e);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
       const int n = e / L, b = e - (e / L) * L;
-      CDF pu = cdf_zero(), py = cdf_zero();
+      P2 ux = pzero(), uy = pzero(), yx = pzero(), yy = pzero();
       for (int a = 0; a < L; ++a) {
-        const CDF gm = ga[a * L + b];
-        cdf_mac(pu, Us[n * L + a], gm);
-        cdf_mac(py, Ys[n * L + a], gm);
+        const CDF& g = ga[a * L + b];
+        pmac_coef(ux, uy, g, Us[n * L + a], m1);
+        pmac_coef(yx, yy, g, Ys[n * L + a], m1);
       }
       const size_t q = e0 + e;
-      const double2 pd = d2_of(pu), yd = d2_of(py);
+      const double2 pd = p2_join(pcombine(ux, uy, m1)), yd = p2_join(pcombine(yx, yy, m1));
       const Cx<double> pv = ld2(R, q) + Cx<double>{pd.x, pd.y};
       const Cx<double> v = ld2(W, q) + Cx<double>{yd.x, yd.y};
       st2(P, q, pv);
       st2(V, q, v);
-      Vs[e] = cdf_split(v);
+      Vs[e] = p2_split(make_double2(v.re, v.im));
     }
     __syncthreads();
-    gram_chunk_df(Rs, Vs, nr, L, acc);
+    gram_chunk_p2(Rs, Vs, nr, L, gx, gy, m1);
   }
   double2* p = part + (size_t)blockIdx.x * PART_STRIDE;
-  if (threadIdx.x < L * L) p[threadIdx.x] = d2_of(acc);
+  if (threadIdx.x < L * L) p[threadIdx.x] = p2_join(pcombine_conj(gx, gy, m1));
 }
 
 inline int blocks_for(long long rows) {

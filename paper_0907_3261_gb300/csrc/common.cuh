@@ -194,3 +194,62 @@ WD_DEV void cdf_macj(CDF& acc, CDF a, CDF b) {
   df_mac(acc.im, a.re, b.im);
   df_msub(acc.im, a.im, b.re);
 }
+
+// ------------------------------------------------------------------ packed double-float
+// The real and imaginary halves of a double-float complex value in the two lanes of FP32x2
+// instructions (FFMA2/FADD2/FMUL2, each lane an IEEE round-to-nearest operation), which halves
+// the instructions issued: hi = (re.hi, im.hi), lo = (re.lo, im.lo).  Subtractions are FMAs with
+// m1 = (-1, -1) (negation is exact).  A complex product sum  sum_k a_k b_k  is accumulated as
+// X = sum a_k.re (b_k.re, b_k.im) and Y = sum a_k.im (b_k.re, b_k.im), the scalar factor in both
+// lanes, and combined once.
+struct P2 {
+  float2 hi, lo;
+};
+WD_DEV float2 dup(float a) { return make_float2(a, a); }
+WD_DEV P2 pzero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+WD_DEV P2 pswap(P2 z) { return {make_float2(z.hi.y, z.hi.x), make_float2(z.lo.y, z.lo.x)}; }
+
+// s + e = a + sg b exactly in each lane (sg = +1 or -1 per lane); two-sum with the sign folded in.
+WD_DEV void two_sum2(float2 a, float2 b, float2 sg, float2 m1, float2& s, float2& e) {
+  s = __ffma2_rn(sg, b, a);
+  const float2 nbb = __ffma2_rn(s, m1, a);   // a - s: minus the part of sg b that reached s
+  const float2 t1 = __fadd2_rn(s, nbb);      // s - bb
+  const float2 t2 = __ffma2_rn(t1, m1, a);   // a - (s - bb)
+  const float2 t3 = __ffma2_rn(sg, b, nbb);  // sg b - bb
+  e = __fadd2_rn(t2, t3);
+}
+WD_DEV P2 padd(P2 a, P2 b, float2 sg, float2 m1) {   // a + sg b
+  float2 s, e;
+  two_sum2(a.hi, b.hi, sg, m1, s, e);
+  return {s, __fadd2_rn(__ffma2_rn(sg, b.lo, a.lo), e)};
+}
+// (re, im) = X + (-Y.im, Y.re): sum a_k b_k from its two accumulators.
+WD_DEV P2 pcombine(P2 X, P2 Y, float2 m1) { return padd(X, pswap(Y), make_float2(-1.f, 1.f), m1); }
+// (re, im) = X + (Y.im, -Y.re): sum conj(a_k) b_k from its two accumulators.
+WD_DEV P2 pcombine_conj(P2 X, P2 Y, float2 m1) {
+  return padd(X, pswap(Y), make_float2(1.f, -1.f), m1);
+}
+// hi + lo renormalised so that |lo| <= ulp(hi)/2, in both lanes.
+WD_DEV P2 pnorm(P2 z, float2 m1) {
+  const float2 s = __fadd2_rn(z.hi, z.lo);
+  return {s, __ffma2_rn(__ffma2_rn(z.hi, m1, s), m1, z.lo)};   // lo - (s - hi)
+}
+// acc + a b for a double-float factor a = ahi + alo given per lane (nahi = -ahi), b packed.
+WD_DEV void pmac_dd(P2& acc, float2 ahi, float2 nahi, float2 alo, P2 b, float2 m1) {
+  const float2 np = __fmul2_rn(nahi, b.hi);   // -(ahi b.hi), rounded
+  float2 e = __ffma2_rn(ahi, b.hi, np);       // its rounding error, exactly
+  e = __ffma2_rn(ahi, b.lo, e);
+  e = __ffma2_rn(alo, b.hi, e);
+  float2 s, t;
+  two_sum2(acc.hi, np, m1, m1, s, t);         // acc.hi - np
+  acc.hi = s;
+  acc.lo = __fadd2_rn(acc.lo, __fadd2_rn(t, e));
+}
+// FP64 (re, im) <-> packed double-float through the bit-field conversions.
+WD_DEV P2 p2_split(double2 v) {
+  const DF r = df_split(v.x), i = df_split(v.y);
+  return {make_float2(r.hi, i.hi), make_float2(r.lo, i.lo)};
+}
+WD_DEV double2 p2_join(P2 z) {   // one FP64 rounding of hi + lo per lane
+  return make_double2(f_widen(z.hi.x) + f_widen(z.lo.x), f_widen(z.hi.y) + f_widen(z.lo.y));
+}

@@ -296,28 +296,8 @@ sweep_df_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4* 
 // im.lo).  Subtractions are FMAs with a (-1, -1) operand (negation is exact).  A complex product
 // sum  sum_b a_b h_b  is accumulated as X = sum ar_b (h_b.re, h_b.im) and Y = sum ai_b (h_b.re,
 // h_b.im) with broadcast operator lanes, and combined once: (re, im) = X + (-Y.im, Y.re).
-struct P2 {
-  float2 hi, lo;
-};
-WD_DEV float2 dup(float a) { return make_float2(a, a); }
-WD_DEV P2 pzero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
-WD_DEV P2 pswap(P2 z) { return {make_float2(z.hi.y, z.hi.x), make_float2(z.lo.y, z.lo.x)}; }
 WD_DEV P2 psel(bool c, P2 a, P2 b) { return c ? a : b; }
 
-// s + e = a + sg b exactly in each lane (sg = +1 or -1 per lane); two-sum with the sign folded in.
-WD_DEV void two_sum2(float2 a, float2 b, float2 sg, float2 m1, float2& s, float2& e) {
-  s = __ffma2_rn(sg, b, a);
-  const float2 nbb = __ffma2_rn(s, m1, a);   // a - s: minus the part of sg b that reached s
-  const float2 t1 = __fadd2_rn(s, nbb);      // s - bb
-  const float2 t2 = __ffma2_rn(t1, m1, a);   // a - (s - bb)
-  const float2 t3 = __ffma2_rn(sg, b, nbb);  // sg b - bb
-  e = __fadd2_rn(t2, t3);
-}
-WD_DEV P2 padd(P2 a, P2 b, float2 sg, float2 m1) {   // a + sg b
-  float2 s, e;
-  two_sum2(a.hi, b.hi, sg, m1, s, e);
-  return {s, __fadd2_rn(__ffma2_rn(sg, b.lo, a.lo), e)};
-}
 // acc + a b for an FP32 operator value a broadcast to both lanes (na = -a).
 WD_DEV void pmac(P2& acc, float2 a, float2 na, P2 b, float2 m1) {
   const float2 np = __fmul2_rn(na, b.hi);   // -(a b.hi), rounded
@@ -334,8 +314,6 @@ WD_DEV P2 pmul(float2 a, float2 na, P2 b) {   // a b as the first term of a sum
   const float2 e = __ffma2_rn(a, b.hi, np);
   return {p, __ffma2_rn(a, b.lo, e)};
 }
-// (re, im) = X + (-Y.im, Y.re): the complex product sum from its two broadcast accumulators.
-WD_DEV P2 pcombine(P2 X, P2 Y, float2 m1) { return padd(X, pswap(Y), make_float2(-1.f, 1.f), m1); }
 
 WD_DEV P2 ldq2(const float4* p) {
   const float4 a = __ldg(p);
