@@ -430,6 +430,11 @@ update_u_df_kernel(const double* __restrict__ P, const double* __restrict__ V, d
   }
 }
 
+// t + z f with two FMAs per real part (the FP64 pipe is this kernel's bound).
+WD_DEV Cx<double> xr_step(Cx<double> t, Cx<double> z, Cx<double> f) {
+  return {fma(-z.im, f.im, fma(z.re, f.re, t.re)), fma(z.im, f.re, fma(z.re, f.im, t.im))};
+}
+
 // Gram entry (a, b) of a chunk: sum_n conj(A[n, a]) B[n, b] into X, Y (see pcombine_conj).  Long
 // sums (thousands of rows per block): both accumulators are renormalised after every product, so
 // their low words never outgrow ulp(hi) and keep ~48-bit accuracy.
@@ -457,7 +462,7 @@ update_xr_df_kernel(double* __restrict__ X, const double* __restrict__ F, const 
   __shared__ double nred[CHE];
   if (st->status != ST_OK) return;
   const float2 m1 = make_float2(-1.f, -1.f);
-  const Cx<double> z = sm(st->zeta);
+  const Cx<double> z = sm(st->zeta), mz = -z;
   P2 gx = pzero(), gy = pzero();
   double nacc = 0.0;
   const long long nchunks = (rows + CH - 1) / CH;
@@ -468,8 +473,8 @@ update_xr_df_kernel(double* __restrict__ X, const double* __restrict__ F, const 
     const size_t e0 = (size_t)r0 * L;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
       const size_t q = e0 + e;
-      const Cx<double> x = ld2(X, q) + cmul(z, ld2(F, q)) + ld2(G, q);
-      const Cx<double> r = ld2(R, q) - cmul(z, ld2(W, q)) - ld2(Y, q);
+      const Cx<double> x = xr_step(ld2(X, q) + ld2(G, q), z, ld2(F, q));
+      const Cx<double> r = xr_step(ld2(R, q) - ld2(Y, q), mz, ld2(W, q));
       st2(X, q, x);
       st2(R, q, r);
       Bs[e] = p2_split(make_double2(r.re, r.im));
