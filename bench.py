@@ -560,7 +560,7 @@ def main():
             "value": round(oracle_tts(k, J_JACOBI, t_apply, t_inv), 3), "unit": "s",
             "cores": cores, "kind": "oracle",
             "sample": (f"oracle A ({t_apply:.2f}s) and A_D^-1 ({t_inv:.2f}s) on the full lattice, "
-                       f"timed on a 16^3x8 slab and scaled x4, times the MVMs of this run's "
+                       f"timed on a 16^3x8 slab and scaled x4, times the MVMs of the plain FP64 method's "
                        f"k={k} iterations at j={J_JACOBI}; L x L steps not included")}
     if rank == 0:
         print(json.dumps(out), flush=True)
