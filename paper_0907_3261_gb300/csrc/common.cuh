@@ -1,4 +1,5 @@
-// Shared device helpers: complex arithmetic on (re, im) pairs, lattice geometry, launch checks.
+// Shared device helpers: complex arithmetic on (re, im) pairs, double-float arithmetic (scalar and
+// packed FP32x2) with its conversions, lattice geometry, launch checks.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -197,8 +198,8 @@ WD_DEV void cdf_macj(CDF& acc, CDF a, CDF b) {
 
 // ------------------------------------------------------------------ packed double-float
 // The real and imaginary halves of a double-float complex value in the two lanes of FP32x2
-// instructions (FFMA2/FADD2/FMUL2, each lane an IEEE round-to-nearest operation), which halves
-// the instructions issued: hi = (re.hi, im.hi), lo = (re.lo, im.lo).  Subtractions are FMAs with
+// instructions (FFMA2/FADD2/FMUL2, each lane an IEEE round-to-nearest operation), so that one
+// instruction does the work of two: hi = (re.hi, im.hi), lo = (re.lo, im.lo).  Subtractions are FMAs with
 // m1 = (-1, -1) (negation is exact).  A complex product sum  sum_k a_k b_k  is accumulated as
 // X = sum a_k.re (b_k.re, b_k.im) and Y = sum a_k.im (b_k.re, b_k.im), the scalar factor in both
 // lanes, and combined once.

@@ -70,7 +70,7 @@ cudaError_t launch_jacobi_bf16_tiled(const Op& op, const void* g_in, const void*
                                      int min_blocks, int staged, cudaStream_t st);
 
 // ---- sweep_df.cu: the double-float preconditioner (FP32 operator, spinors as FP32 pairs).  Its
-// blocks are component-major with one float4 (re.hi, re.lo, im.hi, im.lo) per complex number.
+// blocks are component-major with one float4 (re.hi, im.hi, re.lo, im.lo) per complex number.
 cudaError_t launch_site_inverse_df(const Op& op, const double* u, void* u_df, void* g_df,
                                    double* g64, int L, cudaStream_t st);
 // One sweep with 1 or 2 RHS per thread (dividing L) and `block` (64 or 128) threads per CTA;

@@ -7,12 +7,15 @@
 // the rounding is FP32's.  So these sweeps keep the operator in FP32 and carry every spinor value
 // as an unevaluated sum hi + lo of two FP32 numbers (about 48 significant bits): each product of
 // an FP32 operator entry with a spinor value is split exactly into p + e with an FMA (Dekker), and
-// sums use Knuth's two-sum, so M is linear to ~1e-14.  On GB300, where FP64 runs at 1/61 of the
-// FP32 rate, this is several times faster than FP64 sweeps.
+// sums use Knuth's two-sum, so M is linear to ~1e-13.  On GB300, where FP64 runs at 1/61 of the
+// FP32 rate, this is several times faster than FP64 sweeps.  The scalar kernel does the FP32 work
+// one operation per instruction; the packed one (below) puts the real and imaginary halves in the
+// two lanes of FP32x2 instructions.
 //
 // Blocks are component-major, [spin*3+colour][site][rhs], one float4 (re.hi, im.hi, re.lo,
-// im.lo) per complex number; one thread owns one site and 1 or 2 consecutive right-hand sides.  The first sweep converts the
-// FP64 right-hand side and stores its double-float copy; the last writes FP64 site-major.
+// im.lo) per complex number; one thread owns one site and 1 or 2 consecutive right-hand sides.
+// The first sweep converts the FP64 right-hand side from its bit fields and stores its
+// double-float copy; the last writes FP64 site-major.
 #include <type_traits>
 
 #include "common.cuh"
@@ -292,8 +295,8 @@ sweep_df_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4* 
 // ------------------------------------------------------------------ packed variant
 // The same sweep with the real and imaginary halves of every double-float value in the two lanes
 // of FP32x2 instructions (FFMA2/FADD2/FMUL2, each lane an IEEE round-to-nearest operation), which
-// halves the instructions the scheduler issues.  A value is hi = (re.hi, im.hi), lo = (re.lo,
-// im.lo).  Subtractions are FMAs with a (-1, -1) operand (negation is exact).  A complex product
+// cuts the instructions the scheduler issues by about a third (the FMA pipe then sets the pace).
+// A value is hi = (re.hi, im.hi), lo = (re.lo, im.lo) (helpers in common.cuh).  Subtractions are FMAs with a (-1, -1) operand (negation is exact).  A complex product
 // sum  sum_b a_b h_b  is accumulated as X = sum ar_b (h_b.re, h_b.im) and Y = sum ai_b (h_b.re,
 // h_b.im) with broadcast operator lanes, and combined once: (re, im) = X + (-Y.im, Y.re).
 WD_DEV P2 psel(bool c, P2 a, P2 b) { return c ? a : b; }

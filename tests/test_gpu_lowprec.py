@@ -202,6 +202,25 @@ def test_df_preconditioner_is_linear(wd, dims, L, j):
     assert nonlinearity(wd, ctx, x, y, j, 1) > 100 * DF_LINEARITY_TOL
 
 
+@pytest.mark.parametrize("tile", [(1, 128, 0, 0), (1, 128, 0, 1)])
+def test_df_preconditioner_scales_exactly(wd, tile):
+    """The FP64 <-> double-float conversions work from the IEEE bit fields (exponent, fraction).
+    Scaling the input by 2^k, with every value and intermediate still a normal FP32 number, scales
+    each rounding step exactly, so M(2^k R) = 2^k M(R) bit for bit; M(0) = 0.  A wrong exponent
+    bias or fraction shift in either conversion breaks the equality."""
+    dims, L, j = (4, 4, 4, 8), 5, 4
+    links = I.random_links(dims, 0.3, seed=1)
+    ctx = wd.wd_create(dev(links), dims, 0.125, 1.0)
+    wd.wd_set_tile(ctx, L, *tile, precision=4)
+    R = I.gaussian_block(dims, L, seed=6)
+    G = host(wd.jacobi_precond(ctx, dev(R), j, precision=4))
+    for k in (-30, -7, 9, 60):
+        Gk = host(wd.jacobi_precond(ctx, dev(R * 2.0 ** k), j, precision=4))
+        assert np.array_equal(Gk, G * 2.0 ** k), k
+    Z = host(wd.jacobi_precond(ctx, dev(np.zeros_like(R)), j, precision=4))
+    assert not Z.any()
+
+
 @pytest.mark.parametrize("precision", [4, 5])
 @pytest.mark.parametrize("B_kind,L,j", [("point", 4, 4), ("z4", 12, 4), ("z4", 3, 1)])
 def test_df_solve_matches_fp64_oracle(wd, B_kind, L, j, precision):
