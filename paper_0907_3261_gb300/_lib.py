@@ -220,7 +220,7 @@ def wd_apply(ctx: Context, X, Y=None, stream=None):
 
 def jacobi_precond(ctx: Context, R, j: int, G=None, precision: int = 0, stream=None):
     """G = M R, j Jacobi sweeps from G = 0 (precision 0 = FP64, 1 = FP32 sweeps, 3 = FP32
-    arithmetic on BF16-stored blocks)."""
+    arithmetic on BF16-stored blocks, 4 = double-float sweeps)."""
     pr, L, kr = _ptr_and_L(R, "R")
     if G is None:
         G = _empty_like(R)
@@ -243,9 +243,12 @@ def bbicggr_solve(ctx: Context, B, X=None, j: int = 12, tol: float = 1e-12, maxi
                   history: int = 0, stall_window: int = 16, net=None, stream=None):
     """Solve A X = B by preconditioned block BiCGGR.  Returns (X, info dict).
 
-    ``X`` (if given) holds X_0 and receives the solution; by default X_0 = 0.  Solver outcomes
-    (WD_NOT_CONVERGED, WD_DIVERGED, WD_BREAKDOWN) are reported in ``info["status"]``; argument and
-    CUDA errors raise WDError."""
+    ``X`` (if given) holds X_0 and receives the solution; by default X_0 = 0.  ``precision``
+    picks the preconditioner's arithmetic: 0 FP64 sweeps, 1 FP32 sweeps, 2 as 1 with the direction
+    recurrences in double-float, 3 FP32 arithmetic on BF16 blocks, 4 double-float sweeps, 5 as 4
+    with double-float direction recurrences; in 1-5 a stalled run starts over from X_0 with FP64
+    sweeps (``info["fallbacks"]``).  Solver outcomes (WD_NOT_CONVERGED, WD_DIVERGED, WD_BREAKDOWN)
+    are reported in ``info["status"]``; argument and CUDA errors raise WDError."""
     pb, L, kb = _ptr_and_L(B, "B")
     if X is None:
         if _is_torch(B):
@@ -308,7 +311,8 @@ def wd_profile_read(ctx: Context) -> dict:
 
 def wd_tuned_tile(ctx: Context, L: int, precision: int = 1):
     """(RHS per thread, threads per CTA, min CTAs per SM, staged) of the low-precision sweep for
-    L (precision 1: FP32 blocks, 3: BF16 blocks), or None before the autotuner ran."""
+    L (precision 1: FP32 blocks, 3: BF16 blocks, 4: double-float sweeps, where staged 1 is the
+    packed FP32x2 variant), or None before the autotuner ran."""
     r, b, m, st = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     if lib().wd_tuned_tile(ctx.handle, int(L), int(precision), C.byref(r), C.byref(b),
                            C.byref(m), C.byref(st)) != WD_OK:
@@ -333,7 +337,6 @@ def wd_link_reals(ctx: Context) -> int:
 def wd_set_link_reals(ctx: Context, reals: int) -> None:
     """Choose the link format of the low-precision sweeps (12 needs special unitary links)."""
     _check(lib().wd_set_link_reals(ctx.handle, int(reals)))
-
 
 
 # ---------------------------------------------------------------- learned preconditioner
