@@ -297,3 +297,22 @@ def test_df_dirs_form_across_L_and_kappa(wd, L, kappa):
     X5 = host(X5)
     assert S.true_residual(op, B, X5).max() <= TRUE_RES_TOL
     assert rel(X5, host(X0)) <= SOLVE_X_TOL
+
+
+def test_fp64_solve_scales_exactly(wd):
+    """Every step of the FP64 solver is scale-covariant: the stopping, pivot and stall tests are
+    relative, and scaling B by 2^k scales each FP64 rounding step exactly.  So X(2^k B) = 2^k X(B)
+    bit for bit with the same iteration count.  (The double-float forms are left out: their
+    bit-field conversion keeps the full low word only for |value| >= 2^-79, so a solve scaled far
+    down rounds its smallest block entries differently, though it still converges.)"""
+    dims, L = (4, 4, 4, 8), 4
+    links = I.random_links(dims, 0.3, seed=1)
+    ctx = wd.wd_create(dev(links), dims, 0.125, 1.0)
+    B = I.z4_noise(dims, L, seed=2)
+    X1, i1 = wd.bbicggr_solve(ctx, dev(B), j=4, tol=1e-12, precision=0)
+    X1 = host(X1)
+    assert i1["status"] == wd.WD_OK
+    for k in (-30, 40):
+        Xk, ik = wd.bbicggr_solve(ctx, dev(B * 2.0 ** k), j=4, tol=1e-12, precision=0)
+        assert ik["iters"] == i1["iters"], k
+        assert np.array_equal(host(Xk), X1 * 2.0 ** k), k
