@@ -56,14 +56,21 @@ FORM_NAMES = {"fp64": "plain FP64 Jacobi", "mixed": "mixed: FP32 Jacobi precondi
 # times two half-spinors (6 sums of 3 complex products: 6 x (2 x 3 + 2 x 11) + 12 x 4 x 11) and 24
 # additions into the sums; the row-2 rebuild of the 8 links (30 each); the two 6x6 blocks (12 rows
 # of 1 real and 5 complex products: 6 + 5 x 44 or 28 + 4 x 44 + 22 = 226); U + kappa H (24 split
-# products) and normalising the 24 stored reals (3 each).
+# products) and normalising the 24 stored reals (3 each).  This counts the emulation's work, not
+# the method's: it sets the secondary (ALU) roofline of the double-float sweep only.
 DF_OPS = 8 * (12 * 8 + 6 * (2 * 3 + 2 * 11) + 12 * 4 * 11 + 24 * 8) + 8 * 30 + 12 * 226 \
     + 24 * 11 + 24 * 3
-FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12   # FP32 lane operations per second (2070 MHz)
 METRIC = "time-to-solution at true resid 1e-12 for L RHS; Dslash HBM GB/s vs peak"
 FLOP_APPLY = 1824          # flop per site per RHS of A (1320 hopping + 504 clover)
 FLOP_JACOBI = 1872         # flop per site per RHS of one Jacobi sweep A_D^{-1}(U + kappa H G)
-FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
+
+
+def alu_peaks(sm_count: int, sm_mhz: float):
+    """Derived ALU peaks of the device: FP32 lane operations/s (128 FP32 lanes per SM per clock)
+    and FP64 flop/s (2 FP64 FMAs per SM per clock, 2 flop each), from its SM count and the SM
+    clock sampled during the timed region."""
+    hz = sm_mhz * 1e6
+    return {"fp32_lane_tops": sm_count * 128 * hz / 1e12, "fp64_tflops": sm_count * 4 * hz / 1e12}
 
 
 def algorithmic_bytes(kind: str, L: int, real_bytes: int = 8, link_reals: int = 18,
@@ -447,6 +454,22 @@ def main():
     del Xhs
     block = B.numel() * 16
 
+    # ---- the host link alone: pinned host <-> device copies of one block, for comparison with
+    # the part of e2e that the copies take
+    def copy_gbs(src, dst, reps=5):
+        torch.cuda.synchronize(dev)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(reps):
+            dst.copy_(src, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        return reps * src.numel() * src.element_size() / (c0.elapsed_time(c1) / 1e3) / 1e9
+    Xh_pinned = torch.empty(B.shape, dtype=torch.complex128).pin_memory()
+    host_link = {"pinned_h2d_gbs": round(copy_gbs(Bh, X), 1),
+                 "pinned_d2h_gbs": round(copy_gbs(X, Xh_pinned), 1)}
+    del Xh_pinned
+
     # ---- the other precision forms on the same workload, for comparison (not the value)
     others = []
     col_diff = None
@@ -478,7 +501,10 @@ def main():
                        "max_true_resid": max(i["max_true_resid"] for i in io),
                        "ratio_to_value": round(to / (ms_step / 1e3), 3)})
 
-    # ---- roofline of the dominant kernel class, and of every stencil class
+    # ---- roofline of the dominant kernel class, and of every stencil class.  The primary figure
+    # is the metric's: algorithmic DRAM bytes per launch (each spinor, link and clover block read
+    # or written once) over the CUDA-event launch time, against the measured HBM copy peak.  The
+    # roofline that binds the kernel on this GPU is given beside it (FP64 pipe or FP32 lanes).
     V = int(np.prod(DIMS))
     peaks = {}
     try:
@@ -486,6 +512,13 @@ def main():
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_source = ("MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks
+                  else "fallback 6800 GB/s")
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = int(props.multi_processor_count)
+    clock_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    alu = alu_peaks(sm_count, clock_mhz)
+    alu_source = f"derived: {sm_count} SMs at the sampled median {clock_mhz:.0f} MHz"
     sweep_prec = {"fp64": "fp64", "mixed": "fp32", "bf16": "bf16", "df": "df",
                   "df_dirs": "df"}[args.precision]
     per_kernel = {}
@@ -499,32 +532,29 @@ def main():
         flop_unit = FLOP_APPLY if cls == "dslash_apply" else FLOP_JACOBI
         kind = "dslash_apply" if cls == "dslash_apply" else "dslash_jacobi"
         if f32:   # spinors FP32 or BF16; links and A_D^{-1} FP32
-            nbytes = algorithmic_bytes(kind, L_RHS, 4 if kprec == "fp32" else 2, link_reals, 4) * V
+            per_site = algorithmic_bytes(kind, L_RHS, 4 if kprec == "fp32" else 2, link_reals, 4)
         elif kprec == "df":   # spinors as FP32 pairs; links and A_D^{-1} FP32
-            nbytes = algorithmic_bytes(kind, L_RHS, 8, link_reals, 4) * V
+            per_site = algorithmic_bytes(kind, L_RHS, 8, link_reals, 4)
         else:
-            nbytes = algorithmic_bytes(kind, L_RHS, 8) * V
+            per_site = algorithmic_bytes(kind, L_RHS, 8)
+        nbytes = per_site * V
         tflops = flop_unit * V * L_RHS / avg_s / 1e12
         gbs = nbytes / avg_s / 1e9
+        fig = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+               "frac": round(gbs / hbm_peak, 4), "peak_source": hbm_source,
+               "algorithmic_bytes_per_site": per_site, "units_per_launch": f"{V} sites x L={L_RHS}",
+               "tflops": round(tflops, 3)}
         if kprec == "df":
             tops = DF_OPS * V * L_RHS / avg_s / 1e12
-            fig = {"bound": "alu", "achieved": round(tops, 3), "peak": round(FP32_PEAK_TOPS, 2),
-                   "unit": "T FP32 lane ops/s", "frac": round(tops / FP32_PEAK_TOPS, 4),
-                   "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
-                   "fp32_ops_per_site_rhs": DF_OPS, "tflops_fp64_equivalent": round(tflops, 3),
-                   "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                           "frac": round(gbs / hbm_peak, 4)}}
-        elif f32:
-            fig = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                   "frac": round(gbs / hbm_peak, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs",
-                   "tflops_fp32": round(tflops, 3)}
-        else:
-            fig = {"bound": "alu", "achieved": round(tflops, 4),
-                   "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                   "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
-                   "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
-                   "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                           "frac": round(gbs / hbm_peak, 4)}}
+            fig["binding_roofline"] = {
+                "bound": "alu", "achieved": round(tops, 3), "peak": round(alu["fp32_lane_tops"], 2),
+                "unit": "T FP32 lane ops/s", "frac": round(tops / alu["fp32_lane_tops"], 4),
+                "peak_source": alu_source + " x 128 FP32 lanes", "fp32_ops_per_site_rhs": DF_OPS}
+        elif not f32:
+            fig["binding_roofline"] = {
+                "bound": "alu", "achieved": round(tflops, 4), "peak": round(alu["fp64_tflops"], 4),
+                "unit": "TFLOP/s", "frac": round(tflops / alu["fp64_tflops"], 4),
+                "peak_source": alu_source + " x 2 FP64 FMA/clk"}
         fig.update({"kernel": cls, "precision": kprec,
                     "traffic": ncu_traffic(cls, kprec),
                     "algorithmic_bytes_per_launch": nbytes, "flop_per_site_rhs": flop_unit,
@@ -547,7 +577,7 @@ def main():
            "config": dict(config(args), sweep_tile=tile, link_reals=link_reals),
            "roofline": roofline,
            "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": 2 * block,
-                   "d2h_bytes_per_step": block},
+                   "d2h_bytes_per_step": block, "host_link": host_link},
            "gpu_launches": launches, "clocks": clocks,
            "solve": {"status": "ok" if ok else "FAILED", "iters": infos[-1]["iters"],
                      "mvm_paper": infos[-1]["mvm_paper"],

@@ -133,12 +133,15 @@ int jacobi_precond(wd_ctx* ctx, const void* R, void* G, int L, int j, int precis
  * memory, or a latency-bound loop that cannot pay for cudaMalloc/cudaFree and the device
  * synchronisation cudaFree implies.  jacobi_precond takes its ping-pong block from the context's
  * solver workspace (allocated on first use); this variant takes it from a file-scope device array
- * of 32 MiB, which every GPU that loads the library holds until the process exits.
+ * of 32 MiB.  wd_create loads that array on its device, so every GPU on which a context has been
+ * created holds the 32 MiB from wd_create until the process exits (wd_create fails with
+ * WD_ENOMEM if it cannot be loaded).
  *   Limits: 12*V*L <= 2,097,152 complex numbers (e.g. 8^3x16 with L <= 21, 16^3x32 does not fit);
  *   larger blocks return WD_EINVAL.  R and G must be device buffers (WD_EINVAL for host memory,
- *   which would need staging) and must not overlap.
- *   Set-up: the first call on a device, with that device current, looks up the array's device
- *   address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   which would need staging) and must not overlap.  The current device must be the context's
+ *   device (WD_EINVAL otherwise).
+ *   Set-up: every call looks up the array's device address on the current device
+ *   (cudaGetSymbolAddress, which allocates nothing once wd_create has loaded the array).
  *   Sharing: every call on a device uses the same array, which keeps the last call's contents (the
  *   sweeps overwrite it before reading it, so nothing needs clearing).  Calls whose GPU work
  *   overlaps -- on different streams, or from different host threads -- race on the array. */
@@ -152,6 +155,28 @@ int jacobi_precond_noalloc(wd_ctx* ctx, const void* R, void* G, int L, int j, vo
  * filled.  opts may be NULL (defaults); info may be NULL.  Every column of B must be non-zero. */
 int bbicggr_solve(wd_ctx* ctx, const void* B, void* X, int L, int j, double tol,
                   const bbicggr_opts* opts, bbicggr_info* info, void* stream);
+
+/* ---- Block updates of one outer iteration (Sec. 2, algorithm box), on caller-supplied N x L
+ * device blocks of this context's lattice (complex128, 16-byte aligned, the layout above; host
+ * buffers are WD_EINVAL).  They are the updates bbicggr_solve runs, exposed for tests and for
+ * drivers that run the iteration themselves.  L x L matrices are host arrays of L*L complex128,
+ * row-major (entry (a, b) at a*L + b); zeta is a host complex128 (re, im).  precision: 0 = FP64;
+ * 1 = the products with the L x L matrix and the Gram products in double-float arithmetic (the
+ * direction recurrences of bbicggr_opts.precision 2 and 5); the X and R updates and the column
+ * norms are FP64 in both.  Each call synchronises the stream.  Output blocks must not overlap the
+ * inputs (X and R are updated in place in bb_update_xr).
+ *   bb_update_u:  U = (P - zeta V) alpha                         (S_k and U_k of the box)
+ *   bb_update_xr: X <- X + zeta F + G,  R <- R - zeta W - Y,  rtr_new = R~_0^H R (new R),
+ *                 rnorm2[i] = ||r_i||^2 (new R); rtr_new and rnorm2 may be NULL
+ *   bb_update_pv: P = R + U gamma,  V = W + Y gamma,  rtv = R~_0^H V (new V); rtv may be NULL */
+int bb_update_u(wd_ctx* ctx, const void* P, const void* V, void* U, int L, const double* zeta,
+                const void* alpha, int precision, void* stream);
+int bb_update_xr(wd_ctx* ctx, void* X, const void* F, const void* G, void* R, const void* W,
+                 const void* Y, const void* Rt, int L, const double* zeta, void* rtr_new,
+                 double* rnorm2, int precision, void* stream);
+int bb_update_pv(wd_ctx* ctx, void* P, void* V, const void* R, const void* W, const void* U,
+                 const void* Y, const void* Rt, int L, const void* gamma, void* rtv,
+                 int precision, void* stream);
 
 /* One solve of a batch (bbicggr_solve_batch).  B and X are device buffers; every job has its own
  * context (jobs may differ in lattice, kappa, c_SW, L, j and precision). */

@@ -124,6 +124,22 @@ def site_diagonal(links: np.ndarray, lat: Lattice, kappa: float, csw: float) -> 
     return AD
 
 
+def hopping_term(U: np.ndarray, lat: Lattice, psi: np.ndarray) -> np.ndarray:
+    """The hopping term of Eq. (1) for links U ([V][4][3][3]):
+    H psi = sum_mu (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^H psi(x-mu)."""
+    g = gamma_matrices()
+    psi = psi.reshape(lat.V, 4, 3, -1)
+    out = np.zeros_like(psi)
+    one = np.eye(4)
+    for mu in range(4):
+        up = np.einsum("vab,vsbl->vsal", U[:, mu], psi[lat.fwd[mu]])
+        out += np.einsum("st,vtal->vsal", one - g[mu], up)
+        U_back = U[lat.bwd[mu], mu]
+        dn = np.einsum("vab,vsbl->vsal", _dag(U_back), psi[lat.bwd[mu]])
+        out += np.einsum("st,vtal->vsal", one + g[mu], dn)
+    return out
+
+
 class WilsonClover:
     """The matrix A of Eq. (1) for given links, kappa and c_SW."""
 
@@ -140,16 +156,7 @@ class WilsonClover:
     # -- pieces of A -----------------------------------------------------------------------
     def hopping(self, psi: np.ndarray) -> np.ndarray:
         """H psi = sum_mu (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^H psi(x-mu)."""
-        psi = psi.reshape(self.lat.V, 4, 3, -1)
-        out = np.zeros_like(psi)
-        one = np.eye(4)
-        for mu in range(4):
-            up = np.einsum("vab,vsbl->vsal", self.U[:, mu], psi[self.lat.fwd[mu]])
-            out += np.einsum("st,vtal->vsal", one - self.g[mu], up)
-            U_back = self.U[self.lat.bwd[mu], mu]
-            dn = np.einsum("vab,vsbl->vsal", _dag(U_back), psi[self.lat.bwd[mu]])
-            out += np.einsum("st,vtal->vsal", one + self.g[mu], dn)
-        return out
+        return hopping_term(self.U, self.lat, psi)
 
     def apply_site_diagonal(self, psi: np.ndarray, inverse: bool = False) -> np.ndarray:
         """A_D psi (or A_D^{-1} psi), site by site with the full 12 x 12 block."""

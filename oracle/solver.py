@@ -85,6 +85,24 @@ def right_multiply(X: np.ndarray, C: np.ndarray) -> np.ndarray:
     return (X.reshape(-1, L) @ C).reshape(X.shape)
 
 
+def direction_u(P, V, zeta, alpha):
+    """U_k = S_k alpha_k with S_k = P_k - zeta_k V_k (Sec. 2, algorithm box)."""
+    S = P - zeta * V                           # S_k = P_k - zeta_k V_k
+    return right_multiply(S, alpha)            # U_k = S_k alpha_k
+
+
+def solution_update(X, R, F, G, W, Y, zeta):
+    """X_{k+1} = X_k + zeta_k F_k + G_k and R_{k+1} = R_k - zeta_k W_k - Y_k (Sec. 2, algorithm
+    box)."""
+    return X + zeta * F + G, R - zeta * W - Y
+
+
+def direction_pv(R_new, Uk, W_new, Y, gamma):
+    """P_{k+1} = R_{k+1} + U_k gamma_k and V_{k+1} = W_{k+1} + Y_k gamma_k (Sec. 2, algorithm
+    box)."""
+    return R_new + right_multiply(Uk, gamma), W_new + right_multiply(Y, gamma)
+
+
 @dataclass
 class SolveResult:
     X: np.ndarray
@@ -136,12 +154,10 @@ def bbicggr(op, B, X0, j, eps, maxit=10000, div_thresh=1e2, on_iter=None):
         if ww == 0:
             return X, BREAKDOWN, k, count[0], column_norms(R) / bnorm, hist
         zeta = np.vdot(W, R) / ww                  # zeta_k = Tr[W^H R] / Tr[W^H W]
-        S = P - zeta * V                           # S_k = P_k - zeta_k V_k
-        Uk = right_multiply(S, alpha)              # U_k = S_k alpha_k
+        Uk = direction_u(P, V, zeta, alpha)        # U_k = (P_k - zeta_k V_k) alpha_k
         G = M(Uk)                                  # G_k = M U_k
         Y = A(G)                                   # Y_k = A G_k
-        X = X + zeta * F + G                       # X_{k+1} = X_k + zeta_k F_k + G_k
-        R_new = R - zeta * W - Y                   # R_{k+1} = R_k - zeta_k W_k - Y_k
+        X, R_new = solution_update(X, R, F, G, W, Y, zeta)   # X_{k+1}, R_{k+1}
         k += 1
         rel = column_norms(R_new) / bnorm
         hist.append(float(np.max(rel)))
@@ -162,8 +178,7 @@ def bbicggr(op, B, X0, j, eps, maxit=10000, div_thresh=1e2, on_iter=None):
         except Breakdown:
             return X, BREAKDOWN, k, count[0], rel, hist
         state.update(F_new=F, W_new=W, gamma=gamma)
-        P = R_new + right_multiply(Uk, gamma)      # P_{k+1} = R_{k+1} + U_k gamma_k
-        V = W + right_multiply(Y, gamma)           # V_{k+1} = W_{k+1} + Y_k gamma_k
+        P, V = direction_pv(R_new, Uk, W, Y, gamma)   # P_{k+1}, V_{k+1}
         state.update(P_new=P, V_new=V)
         if on_iter is not None:
             on_iter(state)

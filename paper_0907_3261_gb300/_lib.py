@@ -110,6 +110,11 @@ def lib():
     L.wd_link_reals.restype = C.c_int
     L.wd_set_link_reals.argtypes = [vp, i]
     L.wd_set_link_reals.restype = C.c_int
+    L.bb_update_u.argtypes = [vp, vp, vp, vp, i, vp, vp, i, vp]
+    L.bb_update_xr.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i, vp, vp, vp, i, vp]
+    L.bb_update_pv.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i, vp, vp, i, vp]
+    for name in ("bb_update_u", "bb_update_xr", "bb_update_pv"):
+        getattr(L, name).restype = C.c_int
     L.wd_profile_name.argtypes = [i]
     L.wd_profile_name.restype = C.c_char_p
     for name in ("wd_create", "wd_apply", "jacobi_precond", "jacobi_precond_noalloc",
@@ -284,6 +289,54 @@ def bbicggr_solve(ctx: Context, B, X=None, j: int = 12, tol: float = 1e-12, maxi
                history=np.array(hist[:info.history_count]), seconds=info.seconds,
                fallbacks=info.fallbacks)
     return X, out
+
+
+def _host_c128(a, shape, what):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128).reshape(shape))
+    return a, C.c_void_p(a.ctypes.data)
+
+
+def bb_update_u(ctx: Context, P, V, U, zeta: complex, alpha, precision: int = 0, stream=None):
+    """U = (P - zeta V) alpha on device blocks (precision 1: double-float products)."""
+    pp, L, k1 = _ptr_and_L(P, "P")
+    pv, _, k2 = _ptr_and_L(V, "V")
+    pu, _, k3 = _ptr_and_L(U, "U")
+    z = np.array([complex(zeta)], dtype=np.complex128)
+    al, pal = _host_c128(alpha, (L, L), "alpha")
+    _check(lib().bb_update_u(ctx.handle, pp, pv, pu, L, C.c_void_p(z.ctypes.data), pal,
+                             int(precision), _stream(stream)))
+    return U
+
+
+def bb_update_xr(ctx: Context, X, F, G, R, W, Y, Rt, zeta: complex, precision: int = 0,
+                 stream=None):
+    """X += zeta F + G, R -= zeta W + Y in place; returns (R~_0^H R, ||r_i||^2) of the new R."""
+    ptrs, keep = [], []
+    for name, b in (("X", X), ("F", F), ("G", G), ("R", R), ("W", W), ("Y", Y), ("Rt", Rt)):
+        p, L, k = _ptr_and_L(b, name)
+        ptrs.append(p)
+        keep.append(k)
+    z = np.array([complex(zeta)], dtype=np.complex128)
+    rtr = np.empty((L, L), dtype=np.complex128)
+    nrm = np.empty(L, dtype=np.float64)
+    _check(lib().bb_update_xr(ctx.handle, *ptrs, L, C.c_void_p(z.ctypes.data),
+                              C.c_void_p(rtr.ctypes.data), C.c_void_p(nrm.ctypes.data),
+                              int(precision), _stream(stream)))
+    return rtr, nrm
+
+
+def bb_update_pv(ctx: Context, P, V, R, W, U, Y, Rt, gamma, precision: int = 0, stream=None):
+    """P = R + U gamma, V = W + Y gamma (P, V written); returns R~_0^H V of the new V."""
+    ptrs, keep = [], []
+    for name, b in (("P", P), ("V", V), ("R", R), ("W", W), ("U", U), ("Y", Y), ("Rt", Rt)):
+        p, L, k = _ptr_and_L(b, name)
+        ptrs.append(p)
+        keep.append(k)
+    ga, pga = _host_c128(gamma, (L, L), "gamma")
+    rtv = np.empty((L, L), dtype=np.complex128)
+    _check(lib().bb_update_pv(ctx.handle, *ptrs, L, pga, C.c_void_p(rtv.ctypes.data),
+                              int(precision), _stream(stream)))
+    return rtv
 
 
 WD_K_COUNT = 15

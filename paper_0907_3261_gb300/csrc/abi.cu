@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <initializer_list>
 #include <new>
 #include <vector>
 
@@ -222,16 +223,23 @@ int check_ptr(const void* p, const char* name) {
   return WD_OK;
 }
 
+// The L x L solver state, the reduction partials (one slot per block of the tall-skinny kernels,
+// whose grid is a multiple of the device's SM count) and the host mirror: independent of L.
+int ensure_state(wd_ctx* c) {
+  CHECK(c->part.ensure((size_t)ts_max_blocks() * PART_STRIDE * sizeof(double2)));
+  if (!c->st) CU(cudaMalloc(&c->st, sizeof(SolverState)));
+  if (!c->bnorm2_dev) CU(cudaMalloc(&c->bnorm2_dev, 2 * WD_LMAX * sizeof(double)));
+  if (!c->hm) CU(cudaMallocHost(&c->hm, sizeof(HostMirror)));
+  return WD_OK;
+}
+
 int ensure_workspace(wd_ctx* c, int L) {
   if (c->L == L && c->st) return WD_OK;
   for (auto& b : c->blk) b.release();
   c->L = 0;
   const size_t bytes = block_bytes(c, L);
   for (int i = 0; i < B_CORE; ++i) CHECK(c->blk[i].ensure(bytes));
-  CHECK(c->part.ensure((size_t)152 * 4 * PART_STRIDE * sizeof(double2)));
-  if (!c->st) CU(cudaMalloc(&c->st, sizeof(SolverState)));
-  if (!c->bnorm2_dev) CU(cudaMalloc(&c->bnorm2_dev, 2 * WD_LMAX * sizeof(double)));
-  if (!c->hm) CU(cudaMallocHost(&c->hm, sizeof(HostMirror)));
+  CHECK(ensure_state(c));
   c->L = L;
   return WD_OK;
 }
@@ -537,6 +545,10 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
 }  // namespace
 
 const Op* wd_ctx_op(const wd_ctx* c) { return &c->op; }
+int wd_ctx_device(const wd_ctx* c) { return c->device; }
+void wd_ctx_count_launches(wd_ctx* c, int cls, int nkernels) {
+  if (cls >= 0 && cls < WD_K_COUNT) c->prof.kernels[cls] += nkernels;
+}
 
 void wd_set_error(const char* fmt, ...) {
   va_list ap;
@@ -648,6 +660,10 @@ int wd_create(wd_ctx** out, const void* links, const int dims[4], double kappa, 
   wd_ctx* c = new (std::nothrow) wd_ctx();
   if (!c) { set_err("host allocation failed"); return WD_ENOMEM; }
   cudaGetDevice(&c->device);
+  // The static scratch array of jacobi_precond_noalloc is loaded on this device now, so that it
+  // is never allocated later inside an allocation-free call.
+  int rc0 = noalloc_reserve();
+  if (rc0 != WD_OK) { delete c; return rc0; }
   c->op.g = make_geom(dims);
   c->op.kappa = kappa;
   c->op.csw = csw;
@@ -825,6 +841,97 @@ int jacobi_precond(wd_ctx* c, const void* R, void* G, int L, int j, int precisio
   if (!g_dev) CU(cudaMemcpyAsync(G, gd, bytes, cudaMemcpyDeviceToHost, s));
   if (staged_r || !g_dev) CU(cudaStreamSynchronize(s));
   harvest(c);
+  return WD_OK;
+}
+
+// ---- block updates of one outer iteration on caller-supplied device blocks
+namespace {
+int check_update_args(wd_ctx* c, int L, int precision, std::initializer_list<const void*> blocks) {
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  CHECK(check_L(L));
+  if (precision != 0 && precision != 1) {
+    set_err("precision %d not in {0 (FP64), 1 (double-float)}", precision);
+    return WD_EINVAL;
+  }
+  for (const void* p : blocks) {
+    CHECK(check_ptr(p, "block"));
+    if (!is_device_ptr(p)) { set_err("the block updates take device buffers only"); return WD_EINVAL; }
+  }
+  return ensure_state(c);
+}
+
+// Host L x L complex128 coefficients (row-major) into the device solver state.
+int put_coef(wd_ctx* c, double2* dst, const void* host, int L, cudaStream_t s) {
+  if (!host) { set_err("coefficient matrix is NULL"); return WD_EINVAL; }
+  const double2* h = static_cast<const double2*>(host);
+  CU(cudaMemcpyAsync(dst, h, sizeof(double2) * L * L, cudaMemcpyHostToDevice, s));
+  return WD_OK;
+}
+
+int put_zeta(wd_ctx* c, const double* zeta, cudaStream_t s) {
+  if (!zeta) { set_err("zeta is NULL"); return WD_EINVAL; }
+  CU(cudaMemcpyAsync(&c->st->zeta, zeta, sizeof(double2), cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(&c->st->status, 0, sizeof(int), s));
+  return WD_OK;
+}
+}  // namespace
+
+int bb_update_u(wd_ctx* c, const void* P, const void* V, void* U, int L, const double* zeta,
+                const void* alpha, int precision, void* stream) {
+  CHECK(check_update_args(c, L, precision, {P, V, U}));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long rows = (long long)c->op.g.V * 12;
+  CHECK(put_zeta(c, zeta, s));
+  CHECK(put_coef(c, c->st->alpha, alpha, L, s));
+  LAUNCH(WD_K_UPDATE_U, 1,
+         launch_update_u(static_cast<const double*>(P), static_cast<const double*>(V),
+                         static_cast<double*>(U), L, rows, c->st, s, precision == 1));
+  CU(cudaStreamSynchronize(s));
+  harvest(c);
+  return WD_OK;
+}
+
+int bb_update_xr(wd_ctx* c, void* X, const void* F, const void* G, void* R, const void* W,
+                 const void* Y, const void* Rt, int L, const double* zeta, void* rtr_new,
+                 double* rnorm2, int precision, void* stream) {
+  CHECK(check_update_args(c, L, precision, {X, F, G, R, W, Y, Rt}));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long rows = (long long)c->op.g.V * 12;
+  CHECK(put_zeta(c, zeta, s));
+  LAUNCH(WD_K_UPDATE_XR, 2,
+         launch_update_xr(static_cast<double*>(X), static_cast<const double*>(F),
+                          static_cast<const double*>(G), static_cast<double*>(R),
+                          static_cast<const double*>(W), static_cast<const double*>(Y),
+                          static_cast<const double*>(Rt), L, rows,
+                          static_cast<double2*>(c->part.p), c->st, s, precision == 1));
+  SolverState h;
+  CU(cudaMemcpyAsync(&h, c->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  harvest(c);
+  if (rtr_new) std::memcpy(rtr_new, h.rtr_new, sizeof(double2) * L * L);
+  if (rnorm2) std::memcpy(rnorm2, h.rnorm2, sizeof(double) * L);
+  return WD_OK;
+}
+
+int bb_update_pv(wd_ctx* c, void* P, void* V, const void* R, const void* W, const void* U,
+                 const void* Y, const void* Rt, int L, const void* gamma, void* rtv,
+                 int precision, void* stream) {
+  CHECK(check_update_args(c, L, precision, {P, V, R, W, U, Y, Rt}));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long rows = (long long)c->op.g.V * 12;
+  CU(cudaMemsetAsync(&c->st->status, 0, sizeof(int), s));
+  CHECK(put_coef(c, c->st->gamma, gamma, L, s));
+  LAUNCH(WD_K_UPDATE_PV, 2,
+         launch_update_pv(static_cast<double*>(P), static_cast<double*>(V),
+                          static_cast<const double*>(R), static_cast<const double*>(W),
+                          static_cast<const double*>(U), static_cast<const double*>(Y),
+                          static_cast<const double*>(Rt), L, rows,
+                          static_cast<double2*>(c->part.p), c->st, s, precision == 1));
+  SolverState h;
+  CU(cudaMemcpyAsync(&h, c->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  harvest(c);
+  if (rtv) std::memcpy(rtv, h.rtv, sizeof(double2) * L * L);
   return WD_OK;
 }
 

@@ -539,15 +539,37 @@ update_pv_df_kernel(double* __restrict__ P, double* __restrict__ V, const double
   if (threadIdx.x < L * L) p[threadIdx.x] = p2_join(pcombine_conj(gx, gy, m1));
 }
 
+// Four blocks of TS_THREADS per SM, for the current device (its SM count is read once per device).
+constexpr int MAX_DEVICES = 64;
+int g_sm_count[MAX_DEVICES] = {};
+
+int max_blocks() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+    cudaGetLastError();
+    return 4 * 152;
+  }
+  if (!g_sm_count[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 152;
+    }
+    g_sm_count[dev] = n;
+  }
+  return 4 * g_sm_count[dev];
+}
+
 inline int blocks_for(long long rows) {
   const long long nchunks = (rows + CH - 1) / CH;
-  const long long cap = 152LL * 4;
+  const long long cap = max_blocks();
   return (int)(nchunks < cap ? (nchunks > 0 ? nchunks : 1) : cap);
 }
 
 }  // namespace
 
 int ts_blocks(long long rows) { return blocks_for(rows); }
+int ts_max_blocks() { return max_blocks(); }
 
 cudaError_t launch_gram(const double* A, const double* B, int L, long long rows, double2* part,
                         SolverState* st, int which, bool norms_of_b, cudaStream_t s) {

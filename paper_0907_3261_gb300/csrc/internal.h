@@ -101,6 +101,7 @@ enum { ST_OK = 0, ST_ALPHA_SINGULAR = 1, ST_GAMMA_SINGULAR = 2, ST_ZETA_BAD = 3 
 // Partial-sum slots per block of the reduction kernels.
 constexpr int PART_STRIDE = WD_LMAX * WD_LMAX + WD_LMAX;
 int ts_blocks(long long rows);   // grid size of the tall-skinny kernels for `rows` rows
+int ts_max_blocks();             // largest such grid on the current device (4 x its SM count)
 
 // Which L x L result a gram pass writes.
 enum { GRAM_RTR = 0, GRAM_RTR_NEW = 1, GRAM_RTV = 2 };
@@ -128,7 +129,15 @@ cudaError_t launch_update_pv(double* P, double* V, const double* R, const double
 // ---- abi.cu helpers for other translation units
 struct wd_ctx;
 const Op* wd_ctx_op(const wd_ctx* ctx);
+int wd_ctx_device(const wd_ctx* ctx);   // the device the context was created on
+// Counts `nkernels` launches of class `cls` (WD_K_*) in the context's instrumentation.
+void wd_ctx_count_launches(wd_ctx* ctx, int cls, int nkernels);
 void wd_set_error(const char* fmt, ...);
+
+// ---- noalloc.cu
+// Loads the static scratch array of jacobi_precond_noalloc on the current device (resolving its
+// address forces the module, and with it the array, to be loaded); WD_OK or an error code.
+int noalloc_reserve(void);
 
 // ---- net.cu: the learned preconditioner (activations component-major per channel)
 cudaError_t net_launch_layer(const Op& op, const float* in, float* out, const float2* W, int cin,

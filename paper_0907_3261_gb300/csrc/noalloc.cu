@@ -4,10 +4,10 @@
 // owns the free device memory (an outside cudaMalloc can fail or fragment it), or a latency-bound
 // loop that cannot afford cudaMalloc/cudaFree and the device synchronisation cudaFree implies.
 // jacobi_precond itself takes its ping-pong block from the context's solver workspace, which it
-// allocates on first use.  This variant instead takes that block from the file-scope array below,
-// which every GPU that loads the library holds until the process exits.
+// allocates on first use.  This variant instead takes that block from the file-scope array below.
+// wd_create loads the array on its device (noalloc_reserve), so every GPU on which a context has
+// been created holds the 32 MiB from then until the process exits.
 #include <cstdint>
-#include <mutex>
 
 #include "../../include/bbicggr.h"
 #include "internal.h"
@@ -20,31 +20,20 @@ constexpr size_t NOALLOC_SCRATCH_DOUBLES = size_t(4) << 20;
 constexpr long long NOALLOC_MAX_ELEMENTS = (long long)(NOALLOC_SCRATCH_DOUBLES / 2);
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_setup_mutex;
-double* g_scratch_ptr[MAX_DEVICES] = {};   // device address of g_noalloc_scratch, per device
-
-// Device address of the scratch array on the current device (once per device).  In host code the
-// name g_noalloc_scratch is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress with that device current.
+// Device address of the scratch array on the current device.  In host code the name
+// g_noalloc_scratch is only a host-side stand-in, so the address comes from cudaGetSymbolAddress
+// with that device current.  It is looked up on every call rather than cached: once the module is
+// loaded the lookup allocates nothing and is cheap, and a cached address would go stale if the
+// device's primary context were reset and the module reloaded elsewhere.
 int scratch_for_current_device(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
-    wd_set_error("jacobi_precond_noalloc: no usable current device (%s)", cudaGetErrorString(e));
-    return WD_ECUDA;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    wd_set_error("jacobi_precond_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? WD_ENOMEM : WD_ECUDA;
   }
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      wd_set_error("jacobi_precond_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return WD_ECUDA;
-    }
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<double*>(p);
   return WD_OK;
 }
 
@@ -58,6 +47,15 @@ bool on_device(const void* p) {
 }
 
 }  // namespace
+
+// With CUDA's lazy module loading, the module that holds g_noalloc_scratch -- and with it the
+// 32 MiB -- is loaded the first time something on the device refers to it.  wd_create calls this
+// on the context's device so that the array is taken at a predictable point, before a caller's
+// caching allocator may have claimed the free memory, and never inside a later call.
+int noalloc_reserve(void) {
+  double* p = nullptr;
+  return scratch_for_current_device(&p);
+}
 
 extern "C" int jacobi_precond_noalloc(wd_ctx* ctx, const void* R, void* G, int L, int j,
                                       void* stream) {
@@ -80,6 +78,13 @@ extern "C" int jacobi_precond_noalloc(wd_ctx* ctx, const void* R, void* G, int L
                  "scratch of %lld (32 MiB); use jacobi_precond", elems, NOALLOC_MAX_ELEMENTS);
     return WD_EINVAL;
   }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != wd_ctx_device(ctx)) {
+    cudaGetLastError();
+    wd_set_error("jacobi_precond_noalloc: the current device (%d) is not the context's device (%d)",
+                 dev, wd_ctx_device(ctx));
+    return WD_EINVAL;
+  }
   double* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != WD_OK) return rc;
@@ -89,13 +94,16 @@ extern "C" int jacobi_precond_noalloc(wd_ctx* ctx, const void* R, void* G, int L
   cudaError_t e = cudaSuccess;
   if (j == 0) {
     e = cudaMemcpyAsync(g, r, (size_t)elems * 16, cudaMemcpyDeviceToDevice, s);
+    wd_ctx_count_launches(ctx, WD_K_COPY, 0);
   } else {
     // j sweeps alternate between two blocks; start in G when j is odd so the last lands in G.
     double* cur = (j % 2 == 1) ? g : scratch;
     double* nxt = (j % 2 == 1) ? scratch : g;
     e = launch_site_inverse_f64(op, r, cur, L, s);
+    wd_ctx_count_launches(ctx, WD_K_SITE_INV, 1);
     for (int i = 1; i < j && e == cudaSuccess; ++i) {
       e = launch_jacobi_f64(op, cur, r, nxt, L, s);
+      wd_ctx_count_launches(ctx, WD_K_JACOBI, 1);
       double* t = cur;
       cur = nxt;
       nxt = t;

@@ -200,3 +200,61 @@ def solver_invariant_error(bbicggr, op, B, j, eps=1e-12, maxit=300):
         return np.inf
     note(np.linalg.norm(np.linalg.solve(A, flat(B)) - flat(X)) / np.linalg.norm(flat(X)) * 1e-2)
     return worst[0]
+
+
+def dense_hopping_from_entries(links, dims):
+    """The N x N hopping matrix H written entry by entry from its definition, with the stated
+    chiral basis: the 12 x 12 block of row site x and column site x + mu is (1 - gamma_mu) (x)
+    U_mu(x), that of column site x - mu is (1 + gamma_mu) (x) U_mu(x - mu)^H; blocks add where two
+    neighbours coincide (extent 2).  Neighbours come from explicit periodic coordinate arithmetic,
+    not from the oracle's neighbour tables."""
+    dims = tuple(int(d) for d in dims)
+    lx, ly, lz, lt = dims
+    V = lx * ly * lz * lt
+    U = np.asarray(links).reshape(V, 4, 3, 3)
+    g = chiral_basis()
+    one = np.eye(4)
+    c = coords(dims)
+    H = np.zeros((12 * V, 12 * V), dtype=complex)
+
+    def site(cc):
+        return int(cc[0] + lx * (cc[1] + ly * (cc[2] + lz * cc[3])))
+
+    for x in range(V):
+        for mu in range(4):
+            up = c[x].copy()
+            up[mu] = (up[mu] + 1) % dims[mu]
+            dn = c[x].copy()
+            dn[mu] = (dn[mu] - 1) % dims[mu]
+            y, z = site(up), site(dn)
+            H[12 * x:12 * x + 12, 12 * y:12 * y + 12] += np.kron(one - g[mu], U[x, mu])
+            H[12 * x:12 * x + 12, 12 * z:12 * z + 12] += np.kron(one + g[mu], U[z, mu].conj().T)
+    return H
+
+
+def block_diagonal(blocks):
+    """The N x N matrix with the given 12 x 12 site blocks ([V][12][12]) on its diagonal."""
+    V = blocks.shape[0]
+    D = np.zeros((12 * V, 12 * V), dtype=complex)
+    for v in range(V):
+        D[12 * v:12 * v + 12, 12 * v:12 * v + 12] = blocks[v]
+    return D
+
+
+def fp32_midpoint_distance(values):
+    """For every non-zero real or imaginary part x of ``values``: |x - m| for the FP32 rounding
+    midpoint m (halfway between two adjacent FP32 numbers) nearest to x.  Two FP64 computations of
+    the same quantity that differ by less than this round to the same FP32 number."""
+    x = np.concatenate([np.ravel(np.real(values)), np.ravel(np.imag(values))]).astype(np.float64)
+    x = x[x != 0.0]
+    f = x.astype(np.float32)
+    up = np.nextafter(f, np.float32(np.inf)).astype(np.float64)
+    dn = np.nextafter(f, np.float32(-np.inf)).astype(np.float64)
+    f = f.astype(np.float64)
+    return x, np.minimum(np.abs(x - 0.5 * (f + up)), np.abs(x - 0.5 * (f + dn)))
+
+
+def fp32_rounding_margin(values):
+    """Smallest midpoint distance (fp32_midpoint_distance) relative to |x|; inf if all are 0."""
+    x, d = fp32_midpoint_distance(values)
+    return float(np.min(d / np.abs(x))) if x.size else np.inf

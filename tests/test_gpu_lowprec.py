@@ -316,3 +316,21 @@ def test_fp64_solve_scales_exactly(wd):
         Xk, ik = wd.bbicggr_solve(ctx, dev(B * 2.0 ** k), j=4, tol=1e-12, precision=0)
         assert ik["iters"] == i1["iters"], k
         assert np.array_equal(host(Xk), X1 * 2.0 ** k), k
+
+
+def test_precision2_solve_scaled_far_down(wd):
+    """B scaled by 2^-30: the double-float direction recurrences (precision 2) still converge in
+    the unscaled iteration count to true residual <= 1e-12; their bit-field conversion keeps a
+    full low word down to |value| 2^-79, far below the entries of this solve."""
+    dims, L = (4, 4, 4, 8), 4
+    links = I.random_links(dims, 0.3, seed=1)
+    op = O.WilsonClover(links, dims, 0.125, 1.0)
+    ctx = wd.wd_create(dev(links), dims, 0.125, 1.0)
+    B = I.z4_noise(dims, L, seed=2)
+    X1, i1 = wd.bbicggr_solve(ctx, dev(B), j=4, tol=1e-12, precision=2)
+    Bk = B * 2.0 ** -30
+    Xk, ik = wd.bbicggr_solve(ctx, dev(Bk), j=4, tol=1e-12, precision=2)
+    assert i1["status"] == ik["status"] == wd.WD_OK
+    assert ik["fallbacks"] == 0
+    assert ik["iters"] == i1["iters"]
+    assert S.true_residual(op, Bk, host(Xk)).max() <= TRUE_RES_TOL

@@ -97,6 +97,41 @@ def test_gpu_operator_satisfies_pins(wd):
     assert pins.gauge_covariance_error(make) < 1e-13
 
 
+def test_gpu_clover_inverse_matches_the_abelian_flux_closed_form(wd):
+    """Constant U(1) flux through every plaquette of one plane (pins.abelian_flux_links): the
+    library's A_D must be 1 - kappa c_SW sigma_{mu nu} diag(sin phi, -sin phi, 0) exactly.  One
+    Jacobi sweep from G = 0 applies the library's A_D^{-1}; it is compared with the inverse of
+    that closed form, in all six planes."""
+    dims, kappa, csw = (4, 6, 4, 6), 0.12, 1.7
+    psi = I.gaussian_block(dims, 2, seed=21)
+    V = psi.shape[0]
+    worst = 0.0
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            U, phi = pins.abelian_flux_links(dims, mu, nu)
+            f = np.diag([np.sin(phi), -np.sin(phi), 0.0])
+            AD = np.eye(12) - kappa * csw * np.kron(pins.sigma_closed_form(mu, nu), f)
+            want = np.einsum("ij,vjl->vil", np.linalg.inv(AD), psi.reshape(V, 12, 2))
+            ctx = wd.wd_create(dev(U), dims, kappa, csw)
+            got = host(wd.jacobi_precond(ctx, dev(psi), 1)).reshape(V, 12, 2)
+            worst = max(worst, rel(got, want))
+            wd.wd_destroy(ctx)
+    assert worst < 1e-14
+
+
+def test_jacobi_matches_oracle_j12_8x8x8x16(wd):
+    """The paper's recommended j = 12 (Sec. 3.3) on 8^3 x 16 with L = 12, FP64 sweeps."""
+    dims, L, j = (8, 8, 8, 16), 12, 12
+    links = I.random_links(dims, 0.2, seed=0)
+    op = O.WilsonClover(links, dims, 0.13, 1.0)
+    R = I.z4_noise(dims, L, seed=5)
+    ctx = wd.wd_create(dev(links), dims, 0.13, 1.0)
+    G = host(wd.jacobi_precond(ctx, dev(R), j))
+    G_ref = S.jacobi(op, R, j)
+    assert rel(G, G_ref) <= APPLY_TOL
+    assert max_elem_rel(G, G_ref) <= APPLY_TOL
+
+
 @pytest.mark.parametrize("j", [0, 1, 2, 5])
 @pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 4), ((3, 4, 5, 6), 7)])
 def test_jacobi_matches_oracle(wd, j, dims, L):

@@ -34,12 +34,12 @@ def mutated_module(module, edits):
 
 
 OPERATOR_MUTATIONS = {
-    "swap_projectors": [('one - self.g[mu], up', 'one + self.g[mu], up'),
-                        ('one + self.g[mu], dn', 'one - self.g[mu], dn')],
+    "swap_projectors": [('one - g[mu], up', 'one + g[mu], up'),
+                        ('one + g[mu], dn', 'one - g[mu], dn')],
     "no_dagger_backward": [('_dag(U_back), psi', 'U_back, psi')],
-    "backward_link_at_x": [('U_back = self.U[self.lat.bwd[mu], mu]', 'U_back = self.U[:, mu]')],
-    "transpose_forward": [('"vab,vsbl->vsal", self.U[:, mu]', '"vba,vsbl->vsal", self.U[:, mu]')],
-    "backward_reads_forward": [('psi[self.lat.bwd[mu]])', 'psi[self.lat.fwd[mu]])')],
+    "backward_link_at_x": [('U_back = U[lat.bwd[mu], mu]', 'U_back = U[:, mu]')],
+    "transpose_forward": [('"vab,vsbl->vsal", U[:, mu]', '"vba,vsbl->vsal", U[:, mu]')],
+    "backward_reads_forward": [('psi[lat.bwd[mu]])', 'psi[lat.fwd[mu]])')],
     "hopping_sign": [('(psi) - self.kappa * self.hopping', '(psi) + self.kappa * self.hopping')],
     "hopping_factor_two": [('(psi) - self.kappa * self.hopping',
                             '(psi) - 2 * self.kappa * self.hopping')],
@@ -104,11 +104,12 @@ SOLVER_MUTATIONS = {
                               'solve_small(herm_product(Rt, R), herm_product(Rt, V))')],
     "zeta_conjugated": [('zeta = np.vdot(W, R) / ww', 'zeta = np.vdot(R, W) / ww')],
     "s_sign": [('S = P - zeta * V', 'S = P + zeta * V')],
-    "x_update_drops_zeta": [('X = X + zeta * F + G', 'X = X + F + G')],
-    "r_update_sign": [('R_new = R - zeta * W - Y', 'R_new = R - zeta * W + Y')],
+    "x_update_drops_zeta": [('return X + zeta * F + G, R', 'return X + F + G, R')],
+    "r_update_sign": [('R - zeta * W - Y', 'R - zeta * W + Y')],
     "gamma_missing_zeta": [('herm_product(Rt, R_new) / zeta)', 'herm_product(Rt, R_new))')],
-    "p_update_uses_y": [('P = R_new + right_multiply(Uk, gamma)', 'P = R_new + right_multiply(Y, gamma)')],
-    "v_update_uses_u": [('V = W + right_multiply(Y, gamma)', 'V = W + right_multiply(Uk, gamma)')],
+    "p_update_uses_y": [('return R_new + right_multiply(Uk, gamma)',
+                         'return R_new + right_multiply(Y, gamma)')],
+    "v_update_uses_u": [('W_new + right_multiply(Y, gamma)', 'W_new + right_multiply(Uk, gamma)')],
     "w_not_refreshed": [('W = A(F)                                   # W_{k+1}',
                          'W = W                                      # W_{k+1}')],
 }
@@ -206,3 +207,56 @@ def test_network_mutation_is_caught(kind):
 
 def test_unmutated_network_passes_pins():
     assert network_pin_error(NET.__dict__) < 1e-5
+
+
+# ---------------------------------------------------------------- stored-operator oracle mutations
+from oracle import stored as ST
+
+STORED_MUTATIONS = {
+    "splitting_kappa_sign": [("U + pieces.kappa * pieces.hopping(G)",
+                              "U - pieces.kappa * pieces.hopping(G)")],
+    "splitting_accumulates": [("G = pieces.apply_dinv(U", "G = G + pieces.apply_dinv(U")],
+    "dinv_transposed": [('"vij,vjl->vil", self.Dinv', '"vji,vjl->vil", self.Dinv')],
+    "hermitian_part_without_conj": [("0.5 * (blk + np.conj(np.swapaxes(blk, -1, -2)))",
+                                     "0.5 * (blk + np.swapaxes(blk, -1, -2))")],
+    "one_chirality_only": [("for c in (slice(0, 6), slice(6, 12)):", "for c in (slice(0, 6),):")],
+    "links_not_rounded_kappa_squared": [("float(np.float32(op.kappa))",
+                                         "float(np.float32(op.kappa)) ** 2")],
+}
+
+
+def stored_pin_error(ns):
+    """The pins of tests/test_oracle_stored.py on the mutated module: exact pieces against the
+    pinned polynomial, stored pieces against the dense polynomial on 2^4, and the size of the
+    stored operator's rounding effect (FP32 level, not more)."""
+    try:
+        dims = (2, 3, 2, 3)
+        op = O.WilsonClover(I.random_links(dims, 0.3, seed=2), dims, 0.12, 1.0)
+        R = I.gaussian_block(dims, 2, seed=5)
+        e1 = pins.rel(ns["jacobi_splitting"](ns["exact_pieces"](op), R, 3), S.jacobi(op, R, 3))
+        d2 = (2, 2, 2, 2)
+        op2 = O.WilsonClover(I.random_links(d2, 0.3, seed=0), d2, 0.125, 1.0)
+        pc = ns["fp32_pieces"](op2)
+        H = pins.dense_hopping_from_entries(pc.U, d2)
+        D = pins.block_diagonal(pc.Dinv)
+        u = I.gaussian_block(d2, 2, seed=7).reshape(op2.N, 2)
+        want = D @ u + pc.kappa * D @ H @ (D @ u)
+        got = ns["jacobi_splitting"](pc, u.reshape(op2.lat.V, 4, 3, 2), 2).reshape(op2.N, 2)
+        e2 = pins.rel(got, want)
+        r32 = pins.rel(ns["jacobi_splitting"](pc, u.reshape(op2.lat.V, 4, 3, 2), 4),
+                       S.jacobi(op2, u.reshape(op2.lat.V, 4, 3, 2), 4))
+        e3 = 0.0 if r32 < 1e-6 else np.inf
+        e = max(e1, e2, e3)
+        return e if np.isfinite(e) else np.inf
+    except Exception:
+        return np.inf
+
+
+@pytest.mark.parametrize("kind", sorted(STORED_MUTATIONS))
+def test_stored_mutation_is_caught(kind):
+    ns = mutated_module(ST, STORED_MUTATIONS[kind])
+    assert stored_pin_error(ns) > PIN_TOL
+
+
+def test_unmutated_stored_passes_pins():
+    assert stored_pin_error(ST.__dict__) < 1e-13
