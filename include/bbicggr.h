@@ -264,7 +264,10 @@ const char* wd_profile_name(int kernel_class);
 
 /* Tile of the low-precision Jacobi sweep chosen by the autotuner for this L and storage
  * (precision 1: FP32 blocks, 3: BF16 blocks, 4: double-float sweeps, which take 1 or 2 RHS per
- * thread in 128-thread CTAs, and staged 1 for the packed FP32x2 variant with 1 RHS per thread):
+ * thread in 128-thread CTAs, staged 1 for the packed FP32x2 variant with 1 RHS per thread, and
+ * staged 2 for the packed variant whose link and clover products are summed exactly on a fixed
+ * grid per hop and per clover block -- offered only when every link has rows and columns of norm
+ * at most 1, as unitary links do):
  * RHS per thread, threads per CTA, the minimum
  * resident CTAs per SM the kernel was compiled for (0: none; 8: at most 128 registers a thread),
  * and whether each direction's neighbour data is staged in shared memory (cp.async, two stages)
@@ -277,7 +280,8 @@ int wd_tuned_tile(const wd_ctx* ctx, int L, int precision, int* rhs_per_thread, 
  * min_blocks 0 (or, with block 64, 8, or 12 with one RHS per thread: at most 80 registers) and
  * staged 0; rhs_per_thread 0 with block 128 (the stencil of
  * every (site, rhs) pair split over two warps); or staged 1 with rhs_per_thread 2, block 64 and
- * min_blocks 0. */
+ * min_blocks 0.  Double-float sweeps (precision 4): rhs_per_thread 1 or 2 with block 128,
+ * min_blocks 0 and staged 0, or rhs_per_thread 1 with staged 1 or 2 (2: unitary links only). */
 int wd_set_tile(wd_ctx* ctx, int L, int precision, int rhs_per_thread, int block, int min_blocks,
                 int staged);
 

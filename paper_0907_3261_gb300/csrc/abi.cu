@@ -304,13 +304,15 @@ int ensure_workspace_df(wd_ctx* c, int L, cudaStream_t s) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
-  static const int cand[][2] = {{1, 0}, {2, 0}, {1, 1}};   // (RHS per thread, packed)
+  // (RHS per thread, packed): scalar, scalar with 2 RHS, packed FP32x2, packed with grid sums
+  static const int cand[][2] = {{1, 0}, {2, 0}, {1, 1}, {1, 2}};
   float best = 1e30f;
   int best_i = 0;
   cudaError_t err = cudaSuccess;
-  for (int i = 0; i < 3 && err == cudaSuccess; ++i) {
+  for (int i = 0; i < 4 && err == cudaSuccess; ++i) {
     const int r = cand[i][0], pk = cand[i][1];
     if (L % r != 0) continue;
+    if (pk == 2 && !c->op.links_unitary) continue;
     err = launch_jacobi_df(c->op, a, u_df, b, nullptr, L, r, 128, pk, s);
     if (err == cudaSuccess) err = cudaEventRecord(e0, s);
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
@@ -595,6 +597,7 @@ void wd_destroy(wd_ctx* c) {
   cudaFree(c->op.clov_inv);
   cudaFree(c->op.links32);
   cudaFree(c->op.clov_inv32);
+  cudaFree(c->op.clov_bound32);
   for (auto& b : c->blk) b.release();
   for (auto& b : c->blk32) b.release();
   c->part.release();
@@ -618,19 +621,23 @@ static int create_impl(wd_ctx* c, const void* links, const int dims[4], cudaStre
   CU(cudaMalloc(&op.clov_inv, V * 2 * CLOV_REALS * sizeof(double)));
   CU(cudaMalloc(&op.links32, V * 4 * 18 * sizeof(float)));
   CU(cudaMalloc(&op.clov_inv32, V * 2 * CLOV_REALS * sizeof(float)));
+  CU(cudaMalloc(&op.clov_bound32, V * 2 * sizeof(float)));
   CU(cudaMemcpyAsync(op.links, links, lbytes, cudaMemcpyDefault, s));
-  int* flag;   // [0]: a singular A_D block; [1]: a link that is not special unitary
-  CU(cudaMalloc(&flag, 2 * sizeof(int)));
-  CU(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
+  // [0]: a singular A_D block; [1]: a link that is not special unitary; [2]: a link with a row or
+  // column of norm above 1
+  int* flag;
+  CU(cudaMalloc(&flag, 3 * sizeof(int)));
+  CU(cudaMemsetAsync(flag, 0, 3 * sizeof(int), s));
   CU(launch_clover_build(op, flag, s));
   CU(launch_lp_operator_copies(op, flag + 1, s));
-  int h[2] = {0, 0};
-  cudaError_t e = cudaMemcpyAsync(h, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+  int h[3] = {0, 0, 0};
+  cudaError_t e = cudaMemcpyAsync(h, flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(flag);
   CU(e);
   c->links_su3 = h[1] == 0;
   op.link12 = c->links_su3 ? 1 : 0;
+  op.links_unitary = h[2] == 0 ? 1 : 0;
   if (h[0]) {
     set_err("a 6x6 clover block A_D is singular for kappa=%g c_SW=%g", op.kappa, op.csw);
     return WD_BREAKDOWN;
@@ -716,9 +723,11 @@ int wd_set_tile(wd_ctx* c, int L, int precision, int rhs_per_thread, int block, 
   CHECK(check_L(L));
   int st;
   CHECK(tile_storage(precision, &st));
-  if (st == LP_DF) {   // 1 or 2 RHS per thread, 128 threads; staged 1 = packed (1 RHS)
+  if (st == LP_DF) {   // 1 or 2 RHS per thread, 128 threads; staged 1 = packed, 2 = packed with
+                       // grid sums (1 RHS; unitary links)
     if ((rhs_per_thread != 1 && rhs_per_thread != 2) || L % rhs_per_thread != 0 || block != 128 ||
-        min_blocks != 0 || (staged != 0 && staged != 1) || (staged == 1 && rhs_per_thread != 1)) {
+        min_blocks != 0 || staged < 0 || staged > 2 || (staged != 0 && rhs_per_thread != 1) ||
+        (staged == 2 && !c->op.links_unitary)) {
       set_err("double-float tile (%d RHS/thread, %d threads) not available for L = %d",
               rhs_per_thread, block, L);
       return WD_EINVAL;

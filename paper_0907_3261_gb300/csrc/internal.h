@@ -22,6 +22,13 @@ struct Op {
   // 1: the low-precision sweeps read rows 0 and 1 of each FP32 link and rebuild row 2 (the links
   // are special unitary to LINK12_TOL); 0: they read all three rows.
   int link12;
+  // 1: every link's rows and columns have norm at most 1 + LINK12_TOL (unitary links), which the
+  // grid-biased double-float sweep relies on; 0: that sweep is not used.
+  int links_unitary;
+  // [2 chirality][V]: for each site's inverse block D, max over rows i of
+  // max(sum_j |Re D_ij|, sum_j |Im D_ij|), rounded up -- a bound on the partial sums of a row
+  // times a vector in units of the vector's largest real part.
+  float* clov_bound32;
 };
 
 // Largest entry error |row2 - conj(row0 x row1)| of a link that still counts as special unitary.
@@ -43,9 +50,10 @@ cudaError_t launch_site_inverse_f64(const Op& op, const double* u, double* g_out
 enum { LP_F32 = 0, LP_BF16 = 1, LP_DF = 2 };   // LP_DF: the double-float sweep's tile table
 constexpr size_t lp_elem_bytes(int storage) { return storage == LP_BF16 ? 4 : 8; }
 
-// FP32 component-major links and A_D^{-1}; sets *not_su3 (device) when some link is not special
-// unitary to LINK12_TOL.
-cudaError_t launch_lp_operator_copies(const Op& op, int* not_su3, cudaStream_t st);
+// FP32 component-major links and A_D^{-1} and the row bounds of A_D^{-1}; sets flags[0] (device)
+// when some link is not special unitary to LINK12_TOL and flags[1] when some link has a row or a
+// column of norm above 1 + LINK12_TOL.
+cudaError_t launch_lp_operator_copies(const Op& op, int* flags, cudaStream_t st);
 // First sweep from G = 0: G = A_D^{-1} U, with the low-precision copy of U stored in u_lp.
 cudaError_t launch_site_inverse_lp(const Op& op, int storage, const double* u, void* u_lp,
                                    void* g_lp, double* g64, int L, cudaStream_t st);
@@ -74,7 +82,9 @@ cudaError_t launch_jacobi_bf16_tiled(const Op& op, const void* g_in, const void*
 cudaError_t launch_site_inverse_df(const Op& op, const double* u, void* u_df, void* g_df,
                                    double* g64, int L, cudaStream_t st);
 // One sweep with 1 or 2 RHS per thread (dividing L) and `block` (64 or 128) threads per CTA;
-// packed 1 (with 1 RHS per thread) runs the FP32x2 (real, imaginary lanes) variant.
+// packed 1 (with 1 RHS per thread) runs the FP32x2 (real, imaginary lanes) variant, packed 2 the
+// FP32x2 variant whose link and clover products are summed on a fixed grid (needs
+// op.links_unitary).
 cudaError_t launch_jacobi_df(const Op& op, const void* g_in, const void* u_df, void* g_df,
                              double* g64, int L, int rhs_per_thread, int block, int packed,
                              cudaStream_t st);

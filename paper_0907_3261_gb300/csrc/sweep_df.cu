@@ -454,6 +454,186 @@ sweep_df2_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4*
   }
 }
 
+// ------------------------------------------------------------------ packed variant, grid sums
+// The same sweep with the link and clover products summed on a fixed grid instead of by two-sum.
+// Error-free extraction on a grid (Rump, Ogita and Oishi, "Accurate floating-point summation",
+// SIAM J. Sci. Comput. 31, 2008): if the partial sums of  sum_k a_k b_k  stay below 2^(E-1) in
+// magnitude, an FP32 accumulator S started at sigma = 1.5 * 2^E stays in [2^E, 2^(E+1)), where the
+// FP32 numbers are exactly the multiples of g = 2^(E-23).  Then S' = fma(a, b.hi, S) is S plus the
+// product rounded to the grid, with no other rounding, and fma(a, b.hi, S - S') -- S - S' is exact
+// -- is the part of the product below the grid, |.| <= g/2, rounded to 24 bits of itself.  That
+// part and a b.lo go into a plain FP32 sum.  Per product: 5 FP32x2 operations instead of 11, at an
+// error of ~2^-24 g per product instead of an exact high part (see DESIGN: the sum's error stays
+// ~2^-44 of the bound, the order of the two-sum form's low-word rounding).
+//   Bounds.  A hop sums three products of a link row (norm <= 1: op.links_unitary) with the
+// projected half-spinor h, so each partial sum is below sqrt(3) m, m = max |h.hi| over the hop's
+// twelve reals: E = e(m) + 3 (2^e(m) <= m < 2^(e(m)+1)) gives 2^(E-1) = 4 2^e(m) > 2m.  A clover
+// row sums six products; its bound is the stored row sum (op.clov_bound32) times m =
+// max |v.hi| over the block's input, enlarged by 2^-16 to cover the grid roundings.
+
+// dup(1.5 * 2^(e + k)) for 2^e <= m < 2^(e+1) (m >= 0; m = 0 gives 1.5 * 2^(k - 127)).
+WD_DEV float2 grid_bias(float m, int k) {
+  const unsigned eb = __float_as_uint(m) & 0x7F800000u;
+  return dup(__uint_as_float((eb + ((unsigned)k << 23)) | 0x00400000u));
+}
+// (S, Lo) for the first product a b of a grid sum started at sigma.
+WD_DEV void gmul(float2& S, float2& Lo, float2 a, const P2& b, float2 sigma, float2 m1) {
+  S = __ffma2_rn(a, b.hi, sigma);
+  const float2 d = __ffma2_rn(S, m1, sigma);   // sigma - S, exact
+  Lo = __ffma2_rn(a, b.lo, __ffma2_rn(a, b.hi, d));
+}
+// (S, Lo) + a b.
+WD_DEV void gmac(float2& S, float2& Lo, float2 a, const P2& b, float2 m1) {
+  const float2 s = __ffma2_rn(a, b.hi, S);
+  const float2 d = __ffma2_rn(s, m1, S);       // S - s, exact
+  Lo = __ffma2_rn(a, b.lo, Lo);
+  Lo = __fadd2_rn(Lo, __ffma2_rn(a, b.hi, d));
+  S = s;
+}
+WD_DEV float2 fswap(float2 v) { return make_float2(v.y, v.x); }
+// (re, im) = X + (-Y.im, Y.re) for grid sums X = (SX, LX), Y = (SY, LY) started at sigma: the high
+// parts SX - sigma, SY - sigma and their combination are exact (multiples of g below 2^E).
+WD_DEV P2 gcombine(float2 SX, float2 LX, float2 SY, float2 LY, float2 nsigma) {
+  const float2 cs = make_float2(-1.f, 1.f);
+  const float2 xh = __fadd2_rn(SX, nsigma), yh = __fadd2_rn(SY, nsigma);
+  return {__ffma2_rn(cs, fswap(yh), xh), __ffma2_rn(cs, fswap(LY), LX)};
+}
+WD_DEV float habs_max(const P2& z, float m) { return fmaxf(m, fmaxf(fabsf(z.hi.x), fabsf(z.hi.y))); }
+
+// The hopping term H x at (s, r) as hopping2, the link products summed on the hop's grid.
+WD_DEV void hopping3(const float4* __restrict__ x, const float2* __restrict__ links, const Geom& g,
+                     int s, const int c[4], int r, int L, bool link12, P2 au[2][3], P2 ad[2][3],
+                     float2 m1) {
+  const size_t V = (size_t)g.V;
+  const size_t cs = V * L;
+  const float2 one = make_float2(1.f, 1.f);
+#pragma unroll 1
+  for (int d = 0; d < 8; ++d) {
+    const int mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    const int cm = mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
+    const int ext = g.d[mu], str = g.stride[mu];
+    const int sn = fwd ? (cm == ext - 1 ? s - (ext - 1) * str : s + str)
+                       : (cm == 0 ? s + (ext - 1) * str : s - str);
+    const SpinDir sd = spin_dir(d);
+    const float2 dn0 = make_float2(sd.dn[0], sd.dn[1]), dn1 = make_float2(sd.dn[2], sd.dn[3]);
+    const float2 up0 = make_float2(sd.up[0], sd.up[1]), up1 = make_float2(sd.up[2], sd.up[3]);
+    const float4* base = x + (size_t)sn * L + r;
+    const int k0 = sd.cross ? 9 : 6, k1 = sd.cross ? 6 : 9;
+    P2 h0[3], h1[3];
+    float hm = 0.f;
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const P2 u0 = ldq2(base + (0 * 3 + col) * cs), u1 = ldq2(base + (1 * 3 + col) * cs);
+      const P2 x0 = ldq2(base + (k0 + col) * cs), x1 = ldq2(base + (k1 + col) * cs);
+      h0[col] = padd(u0, psel(sd.swap, pswap(x0), x0), dn0, m1);
+      h1[col] = padd(u1, psel(sd.swap, pswap(x1), x1), dn1, m1);
+      hm = habs_max(h0[col], habs_max(h1[col], hm));
+    }
+    const float2 sigma = grid_bias(hm, 3);
+    const float2 nsigma = make_float2(-sigma.x, -sigma.y);
+    Cx<float> m[3][3];
+    link(links + (size_t)mu * 9 * V + (fwd ? s : sn), V, link12, m);
+    if (!fwd) {   // W = m^H
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 3; ++b) {
+          const Cx<float> t = m[a][b];
+          m[a][b] = conj(m[b][a]);
+          m[b][a] = conj(t);
+        }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) m[a][a] = conj(m[a][a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 SX0, LX0, SY0, LY0, SX1, LX1, SY1, LY1;
+      gmul(SX0, LX0, dup(m[a][0].re), h0[0], sigma, m1);
+      gmul(SY0, LY0, dup(m[a][0].im), h0[0], sigma, m1);
+      gmul(SX1, LX1, dup(m[a][0].re), h1[0], sigma, m1);
+      gmul(SY1, LY1, dup(m[a][0].im), h1[0], sigma, m1);
+#pragma unroll
+      for (int b = 1; b < 3; ++b) {
+        const float2 rb = dup(m[a][b].re), ib = dup(m[a][b].im);
+        gmac(SX0, LX0, rb, h0[b], m1);
+        gmac(SY0, LY0, ib, h0[b], m1);
+        gmac(SX1, LX1, rb, h1[b], m1);
+        gmac(SY1, LY1, ib, h1[b], m1);
+      }
+      const P2 w0 = gcombine(SX0, LX0, SY0, LY0, nsigma);
+      const P2 w1 = gcombine(SX1, LX1, SY1, LY1, nsigma);
+      au[0][a] = padd(au[0][a], w0, one, m1);
+      au[1][a] = padd(au[1][a], w1, one, m1);
+      const P2 y0 = psel(sd.cross, w1, w0), y1 = psel(sd.cross, w0, w1);
+      ad[0][a] = padd(ad[0][a], psel(sd.swap, pswap(y0), y0), up0, m1);
+      ad[1][a] = padd(ad[1][a], psel(sd.swap, pswap(y1), y1), up1, m1);
+    }
+  }
+}
+
+// Row i of a packed Hermitian 6x6 FP32 block times v (as herm6_row2), summed on the grid sigma.
+WD_DEV P2 herm6_row3(const float* __restrict__ mat, size_t stride, int i, const P2 v[6],
+                     float2 sigma, float2 nsigma, float2 m1) {
+  float2 SX, LX, SY, LY;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int t = c_h6_off[i][j];
+    const float sg = c_h6_sgn[i][j];
+    const float re = __ldg(mat + t * stride);
+    const float im = sg * __ldg(mat + (t + (sg != 0.f)) * stride);
+    if (j == 0) {
+      gmul(SX, LX, dup(re), v[0], sigma, m1);
+      gmul(SY, LY, dup(im), v[0], sigma, m1);
+    } else {
+      gmac(SX, LX, dup(re), v[j], m1);
+      gmac(SY, LY, dup(im), v[j], m1);
+    }
+  }
+  return gcombine(SX, LX, SY, LY, nsigma);
+}
+
+template <typename TY>
+__global__ void __launch_bounds__(128, 4)
+sweep_df3_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4* __restrict__ u,
+                 const float2* __restrict__ links, const float* __restrict__ clov_inv,
+                 const float* __restrict__ clov_bound, Geom g, int L, float kappa, int link12) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= g.V * L) return;
+  const int s = tid / L;
+  const int r = tid - s * L;
+  const size_t V = (size_t)g.V;
+  const float2 m1 = make_float2(-1.f, -1.f);
+  int c[4];
+  site_coords(g, s, c);
+  P2 au[2][3], ad[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) { au[a][b] = pzero(); ad[a][b] = pzero(); }
+  hopping3(x, links, g, s, c, r, L, link12 != 0, au, ad, m1);
+  const float2 kap = dup(kappa), nkap = dup(-kappa);
+#pragma unroll 1
+  for (int ch = 0; ch < 2; ++ch) {
+    P2 vin[6];
+    float vm = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const int k = ch * 6 + i;
+      vin[i] = ldq2(u + ((size_t)k * V + s) * L + r);
+      pmac(vin[i], kap, nkap, ch == 0 ? au[i / 3][i % 3] : ad[i / 3][i % 3], m1);
+      vm = habs_max(vin[i], vm);
+    }
+    const float bnd = __ldg(clov_bound + (size_t)ch * V + s) * vm * (1.f + 0x1p-16f);
+    const float2 sigma = grid_bias(bnd, 2);
+    const float2 nsigma = make_float2(-sigma.x, -sigma.y);
+    const float* mm = clov_inv + (size_t)ch * CLOV_REALS * V + s;
+#pragma unroll 1
+    for (int i = 0; i < 6; ++i)
+      stq2(at(y, V, L, s, ch * 6 + i, r), herm6_row3(mm, V, i, vin, sigma, nsigma, m1), m1);
+  }
+}
+
 // First sweep from G = 0: stores the double-float copy of the FP64 right-hand side (when u_df is
 // not null) and writes G = A_D^{-1} U.
 template <typename TY>
@@ -518,11 +698,25 @@ cudaError_t launch_jacobi_df(const Op& op, const void* g_in, const void* u_df, v
                              double* g64, int L, int rhs_per_thread, int block, int packed,
                              cudaStream_t st) {
   if ((block != 64 && block != 128) || (rhs_per_thread != 1 && rhs_per_thread != 2) ||
-      L % rhs_per_thread != 0 || (packed && rhs_per_thread != 1))
+      L % rhs_per_thread != 0 || (packed && rhs_per_thread != 1) || packed < 0 || packed > 2 ||
+      (packed == 2 && !op.links_unitary))
     return cudaErrorInvalidValue;
   const float4* x = static_cast<const float4*>(g_in);
   const float4* u = static_cast<const float4*>(u_df);
   float4* gd = static_cast<float4*>(g_df);
+  if (packed == 2) {
+    const unsigned grid = (unsigned)(((long long)op.g.V * L + block - 1) / block);
+    const float2* links = reinterpret_cast<const float2*>(op.links32);
+    if (gd)
+      sweep_df3_kernel<float4><<<grid, block, 0, st>>>(x, gd, u, links, op.clov_inv32,
+                                                       op.clov_bound32, op.g, L, (float)op.kappa,
+                                                       op.link12);
+    else
+      sweep_df3_kernel<double><<<grid, block, 0, st>>>(x, g64, u, links, op.clov_inv32,
+                                                       op.clov_bound32, op.g, L, (float)op.kappa,
+                                                       op.link12);
+    return cudaGetLastError();
+  }
   if (packed) {
     const unsigned grid = (unsigned)(((long long)op.g.V * L + block - 1) / block);
     const float2* links = reinterpret_cast<const float2*>(op.links32);

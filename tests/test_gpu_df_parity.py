@@ -36,7 +36,8 @@ U_64 = 2.0 ** -53
 # few FP64 ulps of the block's scale; an entry closer than this to an FP32 rounding midpoint could
 # round differently on the two sides, so such lattices are not used (see stored_case).
 INVERSE_MARGIN = 1e-14
-TILES = [(1, 128, 0, 0), (2, 128, 0, 0), (1, 128, 0, 1)]   # scalar 1 RHS, scalar 2 RHS, packed
+# scalar 1 RHS, scalar 2 RHS, packed, packed with grid sums
+TILES = [(1, 128, 0, 0), (2, 128, 0, 0), (1, 128, 0, 1), (1, 128, 0, 2)]
 
 
 @pytest.fixture(scope="module")
@@ -213,4 +214,21 @@ def test_update_entry_points_reject_host_blocks_and_bad_precision(wd):
         wd.bb_update_u(ctx, P, P.copy(), np.zeros_like(P), 0.5, np.eye(L))
     with pytest.raises(wd.WDError):
         wd.bb_update_u(ctx, dev(P), dev(P), dev(P), 0.5, np.eye(L), precision=2)
+    wd.wd_destroy(ctx)
+
+
+def test_grid_sum_tile_needs_unitary_links(wd):
+    """The grid-sum sweep bounds each hop's partial sums by the largest projected spinor entry,
+    which needs link rows and columns of norm <= 1.  Links scaled by 1.1 are refused for it, and
+    the autotuner does not pick it."""
+    dims, L = (3, 4, 5, 6), 6
+    links = I.random_links(dims, 0.3, seed=2) * 1.1
+    ctx = wd.wd_create(dev(links), dims, 0.12, 1.0)
+    with pytest.raises(wd.WDError):
+        wd.wd_set_tile(ctx, L, 1, 128, 0, 2, precision=4)
+    R = I.gaussian_block(dims, L, seed=5)
+    G = host(wd.jacobi_precond(ctx, dev(R), 3, precision=4))
+    assert wd.wd_tuned_tile(ctx, L, precision=4)[3] != 2
+    op = O.WilsonClover(links, dims, 0.12, 1.0)
+    assert element_error(G, S.jacobi(op, R, 3)) <= 1e-5
     wd.wd_destroy(ctx)

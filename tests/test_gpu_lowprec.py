@@ -196,13 +196,13 @@ def test_df_preconditioner_is_linear(wd, dims, L, j):
     ctx = wd.wd_create(dev(links), dims, 0.134, 1.0)
     x = I.z4_noise(dims, L, seed=3)
     y = I.gaussian_block(dims, L, seed=4)
-    for tile in ((1, 128, 0, 0), (1, 128, 0, 1)):
+    for tile in ((1, 128, 0, 0), (1, 128, 0, 1), (1, 128, 0, 2)):
         wd.wd_set_tile(ctx, L, *tile, precision=4)
         assert nonlinearity(wd, ctx, x, y, j, 4) <= DF_LINEARITY_TOL
     assert nonlinearity(wd, ctx, x, y, j, 1) > 100 * DF_LINEARITY_TOL
 
 
-@pytest.mark.parametrize("tile", [(1, 128, 0, 0), (1, 128, 0, 1)])
+@pytest.mark.parametrize("tile", [(1, 128, 0, 0), (1, 128, 0, 1), (1, 128, 0, 2)])
 def test_df_preconditioner_scales_exactly(wd, tile):
     """The FP64 <-> double-float conversions work from the IEEE bit fields (exponent, fraction).
     Scaling the input by 2^k, with every value and intermediate still a normal FP32 number, scales
@@ -256,7 +256,7 @@ def test_df_solve_near_critical_needs_no_fallback(wd):
     assert rel(host(Xdf), host(X64)) <= SOLVE_X_TOL
 
 
-@pytest.mark.parametrize("tile", [(1, 128, 0, 0), (2, 128, 0, 0), (1, 128, 0, 1)])
+@pytest.mark.parametrize("tile", [(1, 128, 0, 0), (2, 128, 0, 0), (1, 128, 0, 1), (1, 128, 0, 2)])
 def test_df_sweep_tiles_match_oracle(wd, tile):
     """Both double-float tiles (1 or 2 RHS per thread) compute the same sweep, and the autotuner
     keeps one of them."""
@@ -271,7 +271,8 @@ def test_df_sweep_tiles_match_oracle(wd, tile):
     assert rel(G, S.jacobi(op, R, j)) <= MIXED_TOL
     ctx2 = wd.wd_create(dev(links), dims, 0.12, 1.0)
     G2 = host(wd.jacobi_precond(ctx2, dev(R), j, precision=4))
-    assert wd.wd_tuned_tile(ctx2, L, precision=4) in ((1, 128, 0, 0), (2, 128, 0, 0), (1, 128, 0, 1))
+    assert wd.wd_tuned_tile(ctx2, L, precision=4) in ((1, 128, 0, 0), (2, 128, 0, 0),
+                                                     (1, 128, 0, 1), (1, 128, 0, 2))
     assert rel(G2, G) <= 1e-13          # the tiles differ only in the order of operations
     with pytest.raises(wd.WDError):
         wd.wd_set_tile(ctx, 3, 2, 128, precision=4)     # 2 does not divide L = 3
