@@ -254,3 +254,42 @@ WD_DEV P2 p2_split(double2 v) {
 WD_DEV double2 p2_join(P2 z) {   // one FP64 rounding of hi + lo per lane
   return make_double2(f_widen(z.hi.x) + f_widen(z.lo.x), f_widen(z.hi.y) + f_widen(z.lo.y));
 }
+
+// ------------------------------------------------------------------ grid sums (packed)
+// Error-free extraction on a fixed grid (Rump, Ogita and Oishi, "Accurate floating-point
+// summation", SIAM J. Sci. Comput. 31, 2008): if every partial sum of  sum_k a_k b_k  stays below
+// 2^(E-1) in magnitude, an FP32 accumulator S started at sigma = 1.5 * 2^E stays in [2^E, 2^(E+1)),
+// where the FP32 numbers are exactly the multiples of g = 2^(E-23).  S' = fma(a, b.hi, S) is then S
+// plus the product rounded to the grid, with no other rounding, and fma(a, b.hi, S - S') (S - S'
+// is exact) is the part of the product below the grid, |.| <= g/2, rounded to 24 bits of itself.
+// That part and the products with the low words go into a plain FP32 sum Lo.  Callers choose E
+// from a bound on the partial sums.  Lo grows to a few g over a sum and rounds at 2^-24 of its size,
+// so the sum's error is ~2^-43 of the bound for a handful of terms (the sweep's three- and six-term
+// sums), and grows with the number of terms.
+// dup(1.5 * 2^(e + k)) for 2^e <= m < 2^(e+1) (m >= 0; m = 0 gives 1.5 * 2^(k - 127)).
+WD_DEV float2 grid_bias(float m, int k) {
+  const unsigned eb = __float_as_uint(m) & 0x7F800000u;
+  return dup(__uint_as_float((eb + ((unsigned)k << 23)) | 0x00400000u));
+}
+// (S, Lo) for the first product a b of a grid sum started at sigma.
+WD_DEV void gmul(float2& S, float2& Lo, float2 a, const P2& b, float2 sigma, float2 m1) {
+  S = __ffma2_rn(a, b.hi, sigma);
+  const float2 d = __ffma2_rn(S, m1, sigma);   // sigma - S, exact
+  Lo = __ffma2_rn(a, b.lo, __ffma2_rn(a, b.hi, d));
+}
+// (S, Lo) + a b.
+WD_DEV void gmac(float2& S, float2& Lo, float2 a, const P2& b, float2 m1) {
+  const float2 s = __ffma2_rn(a, b.hi, S);
+  const float2 d = __ffma2_rn(s, m1, S);       // S - s, exact
+  Lo = __ffma2_rn(a, b.lo, Lo);
+  Lo = __fadd2_rn(Lo, __ffma2_rn(a, b.hi, d));
+  S = s;
+}
+WD_DEV float2 fswap(float2 v) { return make_float2(v.y, v.x); }
+// (re, im) = X + (-Y.im, Y.re) for grid sums X = (SX, LX), Y = (SY, LY) started at sigma: the high
+// parts SX - sigma, SY - sigma and their combination are exact (multiples of g below 2^E).
+WD_DEV P2 gcombine(float2 SX, float2 LX, float2 SY, float2 LY, float2 nsigma) {
+  const float2 cs = make_float2(-1.f, 1.f);
+  const float2 xh = __fadd2_rn(SX, nsigma), yh = __fadd2_rn(SY, nsigma);
+  return {__ffma2_rn(cs, fswap(yh), xh), __ffma2_rn(cs, fswap(LY), LX)};
+}

@@ -471,33 +471,6 @@ sweep_df2_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4*
 // row sums six products; its bound is the stored row sum (op.clov_bound32) times m =
 // max |v.hi| over the block's input, enlarged by 2^-16 to cover the grid roundings.
 
-// dup(1.5 * 2^(e + k)) for 2^e <= m < 2^(e+1) (m >= 0; m = 0 gives 1.5 * 2^(k - 127)).
-WD_DEV float2 grid_bias(float m, int k) {
-  const unsigned eb = __float_as_uint(m) & 0x7F800000u;
-  return dup(__uint_as_float((eb + ((unsigned)k << 23)) | 0x00400000u));
-}
-// (S, Lo) for the first product a b of a grid sum started at sigma.
-WD_DEV void gmul(float2& S, float2& Lo, float2 a, const P2& b, float2 sigma, float2 m1) {
-  S = __ffma2_rn(a, b.hi, sigma);
-  const float2 d = __ffma2_rn(S, m1, sigma);   // sigma - S, exact
-  Lo = __ffma2_rn(a, b.lo, __ffma2_rn(a, b.hi, d));
-}
-// (S, Lo) + a b.
-WD_DEV void gmac(float2& S, float2& Lo, float2 a, const P2& b, float2 m1) {
-  const float2 s = __ffma2_rn(a, b.hi, S);
-  const float2 d = __ffma2_rn(s, m1, S);       // S - s, exact
-  Lo = __ffma2_rn(a, b.lo, Lo);
-  Lo = __fadd2_rn(Lo, __ffma2_rn(a, b.hi, d));
-  S = s;
-}
-WD_DEV float2 fswap(float2 v) { return make_float2(v.y, v.x); }
-// (re, im) = X + (-Y.im, Y.re) for grid sums X = (SX, LX), Y = (SY, LY) started at sigma: the high
-// parts SX - sigma, SY - sigma and their combination are exact (multiples of g below 2^E).
-WD_DEV P2 gcombine(float2 SX, float2 LX, float2 SY, float2 LY, float2 nsigma) {
-  const float2 cs = make_float2(-1.f, 1.f);
-  const float2 xh = __fadd2_rn(SX, nsigma), yh = __fadd2_rn(SY, nsigma);
-  return {__ffma2_rn(cs, fswap(yh), xh), __ffma2_rn(cs, fswap(LY), LX)};
-}
 WD_DEV float habs_max(const P2& z, float m) { return fmaxf(m, fmaxf(fabsf(z.hi.x), fabsf(z.hi.y))); }
 
 // The hopping term H x at (s, r) as hopping2, the link products summed on the hop's grid.
