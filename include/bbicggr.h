@@ -36,6 +36,8 @@
 #ifndef BBICGGR_H
 #define BBICGGR_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -292,6 +294,39 @@ int wd_set_tile(wd_ctx* ctx, int L, int precision, int rhs_per_thread, int block
  * check is WD_EINVAL.  The FP64 path and the learned network always read 18 reals. */
 int wd_link_reals(const wd_ctx* ctx, int* reals);
 int wd_set_link_reals(wd_ctx* ctx, int reals);
+
+/* ---- Domain decomposition across ranks (the paper picks the Jacobi preconditioner for its
+ * parallelism, Sec. 2).  The lattice is cut into slabs along t; a rank's context is created with
+ * wd_create on its slab extended by one t-slice on each side (dims {Lx, Ly, Lz, T + 2}, T >= 1
+ * interior slices), the links of the extended slab filled from the neighbouring ranks (the
+ * clover leaves reach one slice out).  Sites of the two halo slices are computed but not owned.
+ * With a domain set:
+ *   - every product with A and every Jacobi sweep that reads neighbours first fills the halo
+ *     slices of its input block from the neighbouring ranks through `exchange`;
+ *   - every Gram product, trace and column norm runs over the interior rows and is summed over
+ *     the ranks through `allreduce`, so every rank solves the same L x L systems and takes the
+ *     same convergence decisions;
+ *   - bbicggr_solve takes B and X as blocks of the extended slab (their halo rows are ignored on
+ *     entry; X's halo rows are overwritten) and must use precision 0 (FP64 Jacobi sweeps) and no
+ *     network; wd_apply exchanges halos of a copy of X; jacobi_precond takes precision 0;
+ *     bbicggr_solve_batch rejects the context; bb_update_* ignore the domain (all rows).
+ * Both callbacks are called from the thread that called the library, with the stream drained.
+ * They return 0 on success; anything else fails the call with WD_ECUDA. */
+typedef struct {
+  /* Halo exchange on host buffers of `bytes` each: send_lo is this rank's first interior slice
+   * (the previous rank's upper halo), send_hi its last interior slice (the next rank's lower
+   * halo); recv_lo receives the previous rank's last interior slice, recv_hi the next rank's
+   * first (periodic in t). */
+  int (*exchange)(const void* send_lo, const void* send_hi, void* recv_lo, void* recv_hi,
+                  size_t bytes, void* user);
+  /* Sum of n doubles over all ranks, in place in the host buffer `buf`; every rank must get the
+   * same result. */
+  int (*allreduce)(double* buf, int n, void* user);
+  void* user;
+} wd_domain;
+/* Sets (dom not NULL, copied) or clears (NULL) the domain of a context.  WD_EINVAL if a callback
+ * is NULL or the slab has fewer than 3 t-slices. */
+int wd_set_domain(wd_ctx* ctx, const wd_domain* dom);
 
 /* Lattice size and parameters of a context (for bindings): dims[4], V, kappa, c_SW. */
 int wd_query(const wd_ctx* ctx, int dims[4], long long* volume, double* kappa, double* csw);

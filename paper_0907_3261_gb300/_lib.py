@@ -48,6 +48,15 @@ class Job(C.Structure):
                 ("j", C.c_int), ("tol", C.c_double), ("opts", Opts), ("info", Info)]
 
 
+EXCHANGE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                          C.c_void_p)
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.POINTER(C.c_double), C.c_int, C.c_void_p)
+
+
+class DomainStruct(C.Structure):
+    _fields_ = [("exchange", EXCHANGE_FN), ("allreduce", ALLREDUCE_FN), ("user", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -55,7 +64,8 @@ def declared_functions() -> list[str]:
     """Names of the functions include/bbicggr.h declares."""
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", text, flags=re.M)))
+    pat = r"^[ \t]*(?:const[ \t]+)?\w+(?:[ \t]+|[ \t]*\*[ \t]*)(\w+)[ \t]*\("
+    return sorted(set(re.findall(pat, text, flags=re.M)))
 
 
 def lib():
@@ -115,6 +125,8 @@ def lib():
     L.bb_update_pv.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i, vp, vp, i, vp]
     for name in ("bb_update_u", "bb_update_xr", "bb_update_pv"):
         getattr(L, name).restype = C.c_int
+    L.wd_set_domain.argtypes = [vp, C.POINTER(DomainStruct)]
+    L.wd_set_domain.restype = C.c_int
     L.wd_profile_name.argtypes = [i]
     L.wd_profile_name.restype = C.c_char_p
     for name in ("wd_create", "wd_apply", "jacobi_precond", "jacobi_precond_noalloc",
@@ -337,6 +349,37 @@ def bb_update_pv(ctx: Context, P, V, R, W, U, Y, Rt, gamma, precision: int = 0, 
     _check(lib().bb_update_pv(ctx.handle, *ptrs, L, pga, C.c_void_p(rtv.ctypes.data),
                               int(precision), _stream(stream)))
     return rtv
+
+
+def wd_set_domain(ctx: Context, exchange, allreduce) -> None:
+    """Make ``ctx`` (built on a t-slab extended by one halo slice on each side) one rank of a
+    domain-decomposed solve.  ``exchange(send_lo, send_hi, recv_lo, recv_hi)`` gets four uint8
+    numpy views of the library's host staging buffers; ``allreduce(buf)`` a float64 view to sum
+    over ranks in place.  An exception in either fails the library call.  ``exchange=None``
+    clears the domain."""
+    if exchange is None:
+        _check(lib().wd_set_domain(ctx.handle, None))
+        ctx._domain = None
+        return
+
+    def ex(a, b, c, d, nbytes, user):
+        try:
+            view = lambda p: np.ctypeslib.as_array((C.c_uint8 * nbytes).from_address(p))
+            exchange(view(a), view(b), view(c), view(d))
+            return 0
+        except Exception:
+            return 1
+
+    def ar(buf, n, user):
+        try:
+            allreduce(np.ctypeslib.as_array(buf, shape=(n,)))
+            return 0
+        except Exception:
+            return 1
+
+    dom = DomainStruct(EXCHANGE_FN(ex), ALLREDUCE_FN(ar), None)
+    _check(lib().wd_set_domain(ctx.handle, C.byref(dom)))
+    ctx._domain = dom          # the callbacks live as long as the context uses them
 
 
 WD_K_COUNT = 15

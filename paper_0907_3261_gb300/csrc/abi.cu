@@ -133,6 +133,12 @@ struct wd_ctx {
   double* ghist = nullptr;        // residual history, ghist_len entries
   int ghist_len = 0;
   cudaStream_t capture_stream = nullptr;
+  // domain decomposition (wd_set_domain): this context is one rank's t-slab with one halo slice on
+  // each side; halo exchanges and sums over ranks go through the caller's callbacks
+  bool dom_on = false;
+  wd_domain dom{};
+  void* dom_host = nullptr;        // pinned staging: 4 halo slices, then the reduction buffer
+  size_t dom_host_bytes = 0;
 };
 
 namespace {
@@ -356,6 +362,73 @@ int stage_input(const void* p, size_t bytes, DevBuf& stage, const double** out, 
   return WD_OK;
 }
 
+// ---- domain decomposition: halo slices and sums over ranks
+// Sites in one t-slice and the number of halo rows (12 per site) at each end of a block.
+long long slice_sites(const wd_ctx* c) {
+  return (long long)c->op.g.d[0] * c->op.g.d[1] * c->op.g.d[2];
+}
+constexpr int DOM_REDUCE_DOUBLES = 2 * WD_LMAX * WD_LMAX + 2 * WD_LMAX;
+
+int dom_staging(wd_ctx* c, int L) {
+  const size_t slice = (size_t)slice_sites(c) * 12 * L * 16;
+  const size_t need = 4 * slice + DOM_REDUCE_DOUBLES * sizeof(double);
+  if (c->dom_host_bytes >= need) return WD_OK;
+  if (c->dom_host) cudaFreeHost(c->dom_host);
+  c->dom_host = nullptr;
+  c->dom_host_bytes = 0;
+  CU(cudaMallocHost(&c->dom_host, need));
+  c->dom_host_bytes = need;
+  return WD_OK;
+}
+
+// Fills the two halo slices of a block (N x L, site-major, the context's extended slab) from the
+// neighbouring ranks: the first and last interior slices go out, the received slices come in.
+int halo_exchange(wd_ctx* c, double* blk, int L, cudaStream_t s) {
+  if (!c->dom_on) return WD_OK;
+  CHECK(dom_staging(c, L));
+  const long long Vs = slice_sites(c), V = c->op.g.V;
+  const size_t slice = (size_t)Vs * 12 * L * 16;
+  const size_t per_site = (size_t)12 * L * 2;   // doubles
+  char* h = static_cast<char*>(c->dom_host);
+  CU(cudaMemcpyAsync(h, blk + (size_t)Vs * per_site, slice, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(h + slice, blk + (size_t)(V - 2 * Vs) * per_site, slice,
+                     cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (c->dom.exchange(h, h + slice, h + 2 * slice, h + 3 * slice, slice, c->dom.user) != 0) {
+    set_err("wd_domain.exchange failed");
+    return WD_ECUDA;
+  }
+  CU(cudaMemcpyAsync(blk, h + 2 * slice, slice, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(blk + (size_t)(V - Vs) * per_site, h + 3 * slice, slice,
+                     cudaMemcpyHostToDevice, s));
+  return WD_OK;
+}
+
+// Sums n doubles of device memory over all ranks, in place.
+int dom_sum(wd_ctx* c, void* dev, int n, cudaStream_t s) {
+  if (!c->dom_on) return WD_OK;
+  CHECK(dom_staging(c, 1));
+  double* h = reinterpret_cast<double*>(static_cast<char*>(c->dom_host) + c->dom_host_bytes -
+                                        DOM_REDUCE_DOUBLES * sizeof(double));
+  CU(cudaMemcpyAsync(h, dev, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (c->dom.allreduce(h, n, c->dom.user) != 0) {
+    set_err("wd_domain.allreduce failed");
+    return WD_ECUDA;
+  }
+  CU(cudaMemcpyAsync(dev, h, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  return WD_OK;
+}
+
+// Rows of the reductions and block updates (the interior of a slab; all rows without a domain),
+// and the offset of the first such row in doubles.
+long long own_rows(const wd_ctx* c) {
+  return 12LL * (c->op.g.V - (c->dom_on ? 2 * slice_sites(c) : 0));
+}
+size_t own_offset(const wd_ctx* c, int L) {
+  return c->dom_on ? (size_t)slice_sites(c) * 12 * L * 2 : 0;
+}
+
 // G = M R with j Jacobi sweeps; `a` and `b` are two FP64 scratch blocks, the result pointer is
 // returned in *res (one of a, b).  j = 0 copies R.  Modes PM_F32 and PM_BF16 run the sweeps in
 // FP32 arithmetic (FP32 links and A_D^{-1}) on blocks stored in FP32 or BF16 and write the last
@@ -427,6 +500,7 @@ int precondition(wd_ctx* c, const double* R, double* a, double* b, double** res,
   double* cur = a;
   double* nxt = b;
   for (int i = 1; i < j; ++i) {
+    CHECK(halo_exchange(c, cur, L, s));
     LAUNCH(WD_K_JACOBI, 1, launch_jacobi_f64(op, cur, R, nxt, L, s));
     if (hop_count) ++*hop_count;
     double* t = cur;
@@ -469,7 +543,10 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
                 double tol, int maxit, double div_thresh, const double* b2, bbicggr_opts* o, int* hist_n,
                 long long* hop_count, RunResult* out, cudaStream_t s) {
   const Op& op = c->op;
-  const long long rows = (long long)op.g.V * 12;
+  const long long rows = own_rows(c);        // the rows this context owns (its slab's interior)
+  const size_t off = own_offset(c, L);
+  auto in = [off](double* p) { return p + off; };
+  auto cin = [off](const double* p) { return p + off; };
   const size_t bytes = block_bytes(c, L);
   double* R = c->blk[B_R].d();
   double* P = c->blk[B_P].d();
@@ -486,11 +563,14 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
   CU(cudaMemsetAsync(&st->status, 0, sizeof(int), s));
 
   // R_0 = B - A X_0;  P_0 = R_0;  R~_0 = R_0
+  CHECK(halo_exchange(c, X, L, s));
   LAUNCH(WD_K_RESID, 1, launch_resid_f64(op, X, B, R, L, s));
   ++*hop_count;
   LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(P, R, bytes, cudaMemcpyDeviceToDevice, s));
   LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(Rt, R, bytes, cudaMemcpyDeviceToDevice, s));
-  LAUNCH(WD_K_GRAM, 2, launch_gram(Rt, R, L, rows, part, st, GRAM_RTR, true, s));
+  LAUNCH(WD_K_GRAM, 2, launch_gram(in(Rt), in(R), L, rows, part, st, GRAM_RTR, true, s));
+  CHECK(dom_sum(c, st->rtr, 2 * L * L, s));
+  CHECK(dom_sum(c, st->rnorm2, L, s));
   CHECK(read_back(c, s));
   double m = max_rel(c->hm->rnorm2, b2, L, out->rec);
   out->k = 0;
@@ -502,11 +582,14 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
   double* res;
   CHECK(precondition(c, R, pF, pT, &res, L, j, precision, hop_count, s));
   if (res != pF) { pT = pF; pF = res; }
+  CHECK(halo_exchange(c, pF, L, s));
   LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pF, W, L, s));
   ++*hop_count;
   LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(V, W, bytes, cudaMemcpyDeviceToDevice, s));
-  LAUNCH(WD_K_TRACE, 2, launch_traces(W, R, L, rows, part, st, s));
-  LAUNCH(WD_K_GRAM, 2, launch_gram(Rt, V, L, rows, part, st, GRAM_RTV, false, s));
+  LAUNCH(WD_K_TRACE, 2, launch_traces(in(W), in(R), L, rows, part, st, s));
+  CHECK(dom_sum(c, &st->trwr, 3, s));
+  LAUNCH(WD_K_GRAM, 2, launch_gram(in(Rt), in(V), L, rows, part, st, GRAM_RTV, false, s));
+  CHECK(dom_sum(c, st->rtv, 2 * L * L, s));
 
   int k = 0;
   double best = m;
@@ -515,12 +598,15 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
   for (;;) {
     if (k >= maxit) { out->status = WD_NOT_CONVERGED; break; }
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_alpha(st, L, s));                       // alpha_k, zeta_k
-    LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(P, V, U, L, rows, st, s, df));           // U_k = (P_k - zeta_k V_k) alpha_k
+    LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(in(P), in(V), in(U), L, rows, st, s, df));           // U_k = (P_k - zeta_k V_k) alpha_k
     CHECK(precondition(c, U, pG, pT, &res, L, j, precision, hop_count, s));   // G_k = M U_k
     if (res != pG) { pT = pG; pG = res; }
+    CHECK(halo_exchange(c, pG, L, s));
     LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pG, Y, L, s));                  // Y_k = A G_k
     ++*hop_count;
-    LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(X, pF, pG, R, W, Y, Rt, L, rows, part, st, s, df));   // X_{k+1}, R_{k+1}
+    LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(in(X), cin(pF), cin(pG), in(R), cin(W), cin(Y), cin(Rt), L, rows, part, st, s, df));   // X_{k+1}, R_{k+1}
+    CHECK(dom_sum(c, st->rtr_new, 2 * L * L, s));
+    CHECK(dom_sum(c, st->rnorm2, L, s));
     CHECK(read_back(c, s));
     if (c->hm->status != ST_OK) { out->status = WD_BREAKDOWN; break; }
     ++k;
@@ -533,11 +619,14 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
     if (stall > 0 && k - k_best >= stall) { out->status = RUN_STALLED; break; }
     CHECK(precondition(c, R, pF, pT, &res, L, j, precision, hop_count, s));   // F_{k+1} = M R_{k+1}
     if (res != pF) { pT = pF; pF = res; }
+    CHECK(halo_exchange(c, pF, L, s));
     LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pF, W, L, s));                  // W_{k+1} = A F_{k+1}
     ++*hop_count;
-    LAUNCH(WD_K_TRACE, 2, launch_traces(W, R, L, rows, part, st, s));          // Tr[W^H R], Tr[W^H W]
+    LAUNCH(WD_K_TRACE, 2, launch_traces(in(W), in(R), L, rows, part, st, s));  // Tr[W^H R], Tr[W^H W]
+    CHECK(dom_sum(c, &st->trwr, 3, s));
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_gamma(st, L, s));                       // gamma_k
-    LAUNCH(WD_K_UPDATE_PV, 2, launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s, df));   // P_{k+1}, V_{k+1}
+    LAUNCH(WD_K_UPDATE_PV, 2, launch_update_pv(in(P), in(V), cin(R), cin(W), cin(U), cin(Y), cin(Rt), L, rows, part, st, s, df));   // P_{k+1}, V_{k+1}
+    CHECK(dom_sum(c, st->rtv, 2 * L * L, s));
   }
   out->k = k;
   return WD_OK;
@@ -609,6 +698,7 @@ void wd_destroy(wd_ctx* c) {
   cudaFree(c->ghist);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   cudaFreeHost(c->hm);
+  if (c->dom_host) cudaFreeHost(c->dom_host);
   delete c;
 }
 
@@ -789,6 +879,19 @@ int wd_set_link_reals(wd_ctx* c, int reals) {
   return WD_OK;
 }
 
+int wd_set_domain(wd_ctx* c, const wd_domain* dom) {
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  if (!dom) { c->dom_on = false; return WD_OK; }
+  if (!dom->exchange || !dom->allreduce) { set_err("wd_domain needs exchange and allreduce"); return WD_EINVAL; }
+  if (c->op.g.d[3] < 3) {
+    set_err("a domain's slab needs Lt >= 3 (one interior slice and a halo slice on each side)");
+    return WD_EINVAL;
+  }
+  c->dom = *dom;
+  c->dom_on = true;
+  return WD_OK;
+}
+
 int wd_query(const wd_ctx* c, int dims[4], long long* volume, double* kappa, double* csw) {
   if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
   if (dims) for (int m = 0; m < 4; ++m) dims[m] = c->op.g.d[m];
@@ -811,6 +914,13 @@ int wd_apply(wd_ctx* c, const void* X, void* Y, int L, void* stream) {
   const bool y_dev = is_device_ptr(Y);
   double* yd = static_cast<double*>(Y);
   if (!y_dev) { CHECK(c->stage_out.ensure(bytes)); yd = c->stage_out.d(); }
+  if (c->dom_on) {   // refresh the halo slices of a copy of X (the caller's X is not written)
+    CHECK(c->stage_in.ensure(bytes));
+    if (xd != c->stage_in.d())
+      LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(c->stage_in.d(), xd, bytes, cudaMemcpyDeviceToDevice, s));
+    xd = c->stage_in.d();
+    CHECK(halo_exchange(c, c->stage_in.d(), L, s));
+  }
   LAUNCH(WD_K_APPLY, 1, launch_apply_f64(c->op, xd, yd, L, s));
   if (!y_dev) CU(cudaMemcpyAsync(Y, yd, bytes, cudaMemcpyDeviceToHost, s));
   if (staged_x || !y_dev) CU(cudaStreamSynchronize(s));
@@ -826,6 +936,10 @@ int jacobi_precond(wd_ctx* c, const void* R, void* G, int L, int j, int precisio
   if (j < 0) { set_err("j = %d < 0", j); return WD_EINVAL; }
   if (precision != PM_F64 && precision != PM_F32 && precision != PM_BF16 && precision != PM_DF) {
     set_err("precision %d not in {0, 1, 3, 4}", precision);
+    return WD_EINVAL;
+  }
+  if (c->dom_on && precision != PM_F64) {
+    set_err("with a domain set, the Jacobi preconditioner runs FP64 sweeps (precision 0)");
     return WD_EINVAL;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -961,10 +1075,15 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     return WD_EINVAL;
   }
   if (o.precision < 0 || o.precision > 5) { set_err("precision %d not in {0, ..., 5}", o.precision); return WD_EINVAL; }
+  if (c->dom_on && (o.precision != 0 || o.net)) {
+    set_err("a domain-decomposed solve takes the FP64 Jacobi preconditioner (precision 0)");
+    return WD_EINVAL;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CHECK(ensure_workspace(c, L));
   const size_t bytes = block_bytes(c, L);
-  const long long rows = (long long)c->op.g.V * 12;
+  const long long rows = own_rows(c);
+  const size_t off = own_offset(c, L);
 
   const double* Bd = static_cast<const double*>(B);
   if (!is_device_ptr(B)) {
@@ -980,7 +1099,8 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     CU(cudaMemcpyAsync(Xd, X, bytes, cudaMemcpyHostToDevice, s));
   }
   double b2[WD_LMAX];
-  LAUNCH(WD_K_COLNORM, 2, launch_colnorms(Bd, L, rows, static_cast<double2*>(c->part.p), c->bnorm2_dev, s));
+  LAUNCH(WD_K_COLNORM, 2, launch_colnorms(Bd + off, L, rows, static_cast<double2*>(c->part.p), c->bnorm2_dev, s));
+  CHECK(dom_sum(c, c->bnorm2_dev, L, s));
   CU(cudaMemcpyAsync(b2, c->bnorm2_dev, L * sizeof(double), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   for (int i = 0; i < L; ++i)
@@ -1024,10 +1144,12 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     if (rr.status == RUN_STALLED) rr.status = WD_NOT_CONVERGED;
     // true residual ||b_i - A x_i|| / ||b_i||
     double* T = c->blk[B_T].d();
+    CHECK(halo_exchange(c, Xd, L, s));
     LAUNCH(WD_K_RESID, 1, launch_resid_f64(c->op, Xd, Bd, T, L, s));
     ++hops;
     double t2[WD_LMAX];
-    LAUNCH(WD_K_COLNORM, 2, launch_colnorms(T, L, rows, static_cast<double2*>(c->part.p), c->bnorm2_dev + WD_LMAX, s));
+    LAUNCH(WD_K_COLNORM, 2, launch_colnorms(T + off, L, rows, static_cast<double2*>(c->part.p), c->bnorm2_dev + WD_LMAX, s));
+    CHECK(dom_sum(c, c->bnorm2_dev + WD_LMAX, L, s));
     CU(cudaMemcpyAsync(t2, c->bnorm2_dev + WD_LMAX, L * sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     mtrue = max_rel(t2, b2, L, true_rel);
@@ -1273,6 +1395,7 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     bbicggr_job& jb = jobs[i];
     wd_ctx* c = jb.ctx;
     if (!c) { set_err("job %d: ctx is NULL", i); return WD_EINVAL; }
+    if (c->dom_on) { set_err("job %d: a domain-decomposed context cannot join a batch", i); return WD_EINVAL; }
     for (int k = 0; k < i; ++k)
       if (jobs[k].ctx == c) { set_err("jobs %d and %d share a context", k, i); return WD_EINVAL; }
     CHECK(check_L(jb.L));

@@ -80,3 +80,50 @@ def test_single_rank_wraps_periodically():
     assert D.slab_range(8, 0, 3) == (0, 3) and D.slab_range(8, 2, 3) == (6, 8)
     with pytest.raises(ValueError):
         D.slab_range(2, 0, 3)
+
+
+def callback_worker(rank, world, port, results):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ex = D.exchange_callback(dist, rank, world)
+    ar = D.allreduce_callback(dist)
+    n = 40
+    send_lo = np.full(n, 10 * rank + 1, dtype=np.uint8)
+    send_hi = np.full(n, 10 * rank + 2, dtype=np.uint8)
+    recv_lo, recv_hi = np.zeros(n, np.uint8), np.zeros(n, np.uint8)
+    for _ in range(2):               # two exchanges in a row reuse the same tags
+        ex(send_lo, send_hi, recv_lo, recv_hi)
+    buf = np.array([float(rank), 1.0, 0.5 * rank])
+    ar(buf)
+    results[rank] = (recv_lo.copy(), recv_hi.copy(), buf)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_domain_callbacks_exchange_halos_and_sum(world):
+    """The callbacks wd_set_domain calls: each rank receives the previous rank's last interior
+    slice as its lower halo and the next rank's first as its upper halo (periodic), and the sum
+    over ranks is the same on every rank."""
+    port = free_port()
+    with mp.Manager() as m:
+        results = m.dict()
+        mp.spawn(callback_worker, args=(world, port, results), nprocs=world, join=True)
+        res = dict(results)
+    for r in range(world):
+        recv_lo, recv_hi, buf = res[r]
+        prev, nxt = (r - 1) % world, (r + 1) % world
+        assert (recv_lo == 10 * prev + 2).all() and (recv_hi == 10 * nxt + 1).all()
+        assert np.array_equal(buf, res[0][2])
+        assert buf[0] == sum(range(world)) and buf[1] == world
+
+
+def test_single_rank_callbacks_wrap():
+    ex, ar = D.exchange_callback(), D.allreduce_callback()
+    lo, hi = np.arange(5, dtype=np.uint8), np.arange(5, 10, dtype=np.uint8)
+    rl, rh = np.zeros(5, np.uint8), np.zeros(5, np.uint8)
+    ex(lo, hi, rl, rh)
+    assert np.array_equal(rl, hi) and np.array_equal(rh, lo)
+    b = np.array([1.5, 2.0])
+    ar(b)
+    assert np.array_equal(b, [1.5, 2.0])
