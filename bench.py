@@ -61,6 +61,14 @@ FORM_NAMES = {"fp64": "plain FP64 Jacobi", "mixed": "mixed: FP32 Jacobi precondi
 # the method's: it sets the secondary (ALU) roofline of the double-float sweep only.
 DF_OPS = 8 * (12 * 8 + 6 * (2 * 3 + 2 * 11) + 12 * 4 * 11 + 24 * 8) + 8 * 30 + 12 * 226 \
     + 24 * 11 + 24 * 3
+# The same count for the grid-sum sweep (the DF tile's staged = 2): per lane a product costs 5
+# operations (4 for the first of a sum) and each complex product sum is combined with 4 lane
+# operations per lane pair.  Each hop: the projection (12 x 8), six complex outputs of two
+# three-term lane-pair sums (6 x (2 x 2 x 14 + 8)), 16 for the grid's bound and the 24 additions
+# into the site sums (24 x 8); the row-2 rebuild (8 x 30); the twelve clover rows of two six-term
+# lane-pair sums (12 x (2 x 2 x 29 + 8)) and 30 for their bounds; U + kappa H and the stores.
+DF_OPS_GRID = 8 * (12 * 8 + 6 * (2 * 2 * 14 + 8) + 16 + 24 * 8) + 8 * 30 \
+    + 12 * (2 * 2 * 29 + 8) + 30 + 24 * 11 + 24 * 3
 METRIC = "time-to-solution at true resid 1e-12 for L RHS; Dslash HBM GB/s vs peak"
 FLOP_APPLY = 1824          # flop per site per RHS of A (1320 hopping + 504 clover)
 FLOP_JACOBI = 1872         # flop per site per RHS of one Jacobi sweep A_D^{-1}(U + kappa H G)
@@ -533,8 +541,13 @@ def main():
 
     # ---- end to end through the C-ABI with pinned host buffers.  Every step gets its own X0 = 0
     # host buffer, prepared before the timed region like B; inside it are the copies of B and X0
-    # in, the solve, and the copy of X out.
+    # in, the solve, and the copy of X out.  Preparing a buffer includes its first transfer: the
+    # first DMA from freshly pinned memory maps its pages (~35 ms for 302 MB on this host, against
+    # ~1.5 ms for every later transfer), which is a cost of allocating the buffer, not of a step.
     Xhs = [torch.zeros(B.shape, dtype=torch.complex128).pin_memory() for _ in range(args.steps)]
+    for Xh in Xhs:
+        X.copy_(Xh, non_blocking=True)
+    torch.cuda.synchronize(dev)
     Bn = Bh.numpy()
     if dist:
         dist.barrier()
@@ -549,6 +562,7 @@ def main():
     # ---- the host link alone: pinned host <-> device copies of one block, for comparison with
     # the part of e2e that the copies take
     def copy_gbs(src, dst, reps=5):
+        dst.copy_(src, non_blocking=True)     # the first transfer maps freshly pinned pages
         torch.cuda.synchronize(dev)
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record(stream)
@@ -613,6 +627,7 @@ def main():
     alu_source = f"derived: {sm_count} SMs at the sampled median {clock_mhz:.0f} MHz"
     sweep_prec = {"fp64": "fp64", "mixed": "fp32", "bf16": "bf16", "df": "df",
                   "df_dirs": "df"}[args.precision]
+    df_tile = wd.wd_tuned_tile(ctx, L_RHS, precision=4) if sweep_prec == "df" else None
     per_kernel = {}
     for cls in ("dslash_jacobi_lp", "dslash_jacobi", "dslash_apply"):
         n, ms = prof.get(cls, (0, 0.0))
@@ -637,11 +652,12 @@ def main():
                "algorithmic_bytes_per_site": per_site, "units_per_launch": f"{V} sites x L={L_RHS}",
                "tflops": round(tflops, 3)}
         if kprec == "df":
-            tops = DF_OPS * V * L_RHS / avg_s / 1e12
+            ops = DF_OPS_GRID if df_tile and df_tile[3] == 2 else DF_OPS
+            tops = ops * V * L_RHS / avg_s / 1e12
             fig["binding_roofline"] = {
                 "bound": "alu", "achieved": round(tops, 3), "peak": round(alu["fp32_lane_tops"], 2),
                 "unit": "T FP32 lane ops/s", "frac": round(tops / alu["fp32_lane_tops"], 4),
-                "peak_source": alu_source + " x 128 FP32 lanes", "fp32_ops_per_site_rhs": DF_OPS}
+                "peak_source": alu_source + " x 128 FP32 lanes", "fp32_ops_per_site_rhs": ops}
         elif not f32:
             fig["binding_roofline"] = {
                 "bound": "alu", "achieved": round(tflops, 4), "peak": round(alu["fp64_tflops"], 4),
