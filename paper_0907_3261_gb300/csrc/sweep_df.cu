@@ -608,32 +608,40 @@ sweep_df3_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4*
 }
 
 // First sweep from G = 0: stores the double-float copy of the FP64 right-hand side (when u_df is
-// not null) and writes G = A_D^{-1} U.
+// not null) and writes G = A_D^{-1} U, the clover rows in packed grid sums (as sweep_df3_kernel;
+// with links that are not unitary the clover row bound still holds, so this needs no check).
 template <typename TY>
 __global__ void __launch_bounds__(128)
 site_inverse_df_kernel(const double* __restrict__ u, float4* __restrict__ u_df, TY* __restrict__ y,
-                       const float* __restrict__ clov_inv, int V, int L) {
+                       const float* __restrict__ clov_inv, const float* __restrict__ clov_bound,
+                       int V, int L) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= V * L) return;
   const int s = tid / L;
   const int r = tid - s * L;
-  const size_t base = 2 * ((size_t)s * 12 * L + r);
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const size_t base = (size_t)s * 12 * L + r;    // complex index of (s, component 0, r)
+  const double2* u2 = reinterpret_cast<const double2*>(u);
 #pragma unroll 1
   for (int ch = 0; ch < 2; ++ch) {
-    C vin[1][6];
+    P2 vin[6];
+    float vm = 0.f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       const int k = ch * 6 + i;
-      vin[0][i] = cdf_split(ldc(u + base + 2 * (size_t)(k * L)));
-      if (u_df) stq(at(u_df, (size_t)V, L, s, k, r), vin[0][i]);
+      vin[i] = p2_split(__ldg(u2 + base + (size_t)k * L));
+      if (u_df)
+        *at(u_df, (size_t)V, L, s, k, r) =
+            make_float4(vin[i].hi.x, vin[i].hi.y, vin[i].lo.x, vin[i].lo.y);
+      vm = habs_max(vin[i], vm);
     }
-    const float* m = clov_inv + (size_t)ch * CLOV_REALS * V + s;
+    const float bnd = __ldg(clov_bound + (size_t)ch * V + s) * vm * (1.f + 0x1p-16f);
+    const float2 sigma = grid_bias(bnd, 2);
+    const float2 nsigma = make_float2(-sigma.x, -sigma.y);
+    const float* mm = clov_inv + (size_t)ch * CLOV_REALS * V + s;
 #pragma unroll 1
-    for (int i = 0; i < 6; ++i) {
-      C out[1];
-      herm6_row<1>(m, (size_t)V, i, vin, out);
-      stq(at(y, (size_t)V, L, s, ch * 6 + i, r), out[0]);
-    }
+    for (int i = 0; i < 6; ++i)
+      stq2(at(y, (size_t)V, L, s, ch * 6 + i, r), herm6_row3(mm, V, i, vin, sigma, nsigma, m1), m1);
   }
 }
 
@@ -645,9 +653,10 @@ cudaError_t launch_site_inverse_df(const Op& op, const double* u, void* u_df, vo
   float4* ud = static_cast<float4*>(u_df);
   if (g_df)
     site_inverse_df_kernel<float4><<<grid, 128, 0, st>>>(u, ud, static_cast<float4*>(g_df),
-                                                         op.clov_inv32, op.g.V, L);
+                                                         op.clov_inv32, op.clov_bound32, op.g.V, L);
   else
-    site_inverse_df_kernel<double><<<grid, 128, 0, st>>>(u, ud, g64, op.clov_inv32, op.g.V, L);
+    site_inverse_df_kernel<double><<<grid, 128, 0, st>>>(u, ud, g64, op.clov_inv32,
+                                                         op.clov_bound32, op.g.V, L);
   return cudaGetLastError();
 }
 
