@@ -458,6 +458,10 @@ def main():
                     help="fix the FP32 sweep tile 'rhs_per_thread,block,min_blocks[,staged]' instead of "
                          "autotuning it (reproducible profiling)")
     ap.add_argument("--bf16-tile", default="", help="the same for the BF16-storage sweep")
+    ap.add_argument("--df-tile", default="",
+                    help="the same for the double-float sweep (e.g. 1,128,0,2: packed, grid sums); "
+                         "a run under a profiler should fix it, since the profiler's per-launch "
+                         "overhead misleads the autotuner's timings")
     ap.add_argument("--link-reals", type=int, default=0, choices=[0, 12, 18],
                     help="link format of the low-precision sweeps (0: the library's choice)")
     ap.add_argument("--no-other-form", action="store_true",
@@ -499,6 +503,8 @@ def main():
         wd.wd_set_tile(ctx, L_RHS, *[int(v) for v in args.fp32_tile.split(",")], precision=1)
     if args.bf16_tile:
         wd.wd_set_tile(ctx, L_RHS, *[int(v) for v in args.bf16_tile.split(",")], precision=3)
+    if args.df_tile:
+        wd.wd_set_tile(ctx, L_RHS, *[int(v) for v in args.df_tile.split(",")], precision=4)
     if args.link_reals:
         wd.wd_set_link_reals(ctx, args.link_reals)
     link_reals = wd.wd_link_reals(ctx)
