@@ -352,14 +352,51 @@ def batch_jobs():
     return [(d, L, 0.115 + 0.009 * i / (len(combos) - 1)) for i, (d, L) in enumerate(combos)]
 
 
-# The batch's kappa stay well below the critical one, where FP32 sweeps keep block BiCGGR converging;
-# precision 2 adds the double-float direction recurrences (bbicggr_opts.precision).
-BATCH_PRECISION = 2
+# Preconditioner mixes of the batch (--batch-mix).  The kappa stay well below the critical one,
+# where FP32 sweeps keep block BiCGGR converging; precision 2 adds the double-float direction
+# recurrences.  "stated" is the mixed-precision plus learned-preconditioner batch: the 8^4 jobs use
+# the gauge-covariant network (FP32 activations; trained in this run on 16 other 8^4
+# configurations, outside the timed region) with j = 8 FP64 Jacobi as its fallback, every other
+# job FP32 sweeps with double-float directions.
+BATCH_J = 8
+BATCH_MIXES = {
+    "stated": "8^4 jobs: learned 4-layer network (FP32 activations, FP64-Jacobi j=8 fallback); "
+              "others: Jacobi j=8 in FP32 with double-float direction recurrences",
+    "jacobi": "Jacobi j=8 in FP32 with double-float direction recurrences",
+    "df": "Jacobi j=8 in double-float with double-float direction recurrences",
+}
+NET_TRAIN_SEEDS = list(range(1, 17))
+NET_TRAIN_KAPPA = 0.12
+NET_TRAIN_STEPS = 600
+
+
+def train_batch_network(wd, I, torch, dev):
+    """The learned preconditioner of the stated mix, trained on (r, A^-1 r) pairs that the plain
+    solver generates on 16 8^4 configurations other than the batch's (seeds 1-16)."""
+    from paper_0907_3261_gb300 import train_net as T
+    t0 = time.perf_counter()
+    pairs = T.make_pairs(wd, I, torch, BATCH_LATTICES[0], NET_TRAIN_KAPPA, CSW, NET_TRAIN_SEEDS,
+                         12, LINK_EPS, 12, dev)
+    net = wd.wd_net_create(4, 4, I.network_weights(4, 4, seed=7, noise=0.01))
+    hist = T.train(wd, net, pairs, NET_TRAIN_STEPS, 3e-3, log_every=0)
+    torch.cuda.synchronize()
+    return net, {"configs": len(NET_TRAIN_SEEDS), "kappa": NET_TRAIN_KAPPA,
+                 "steps": NET_TRAIN_STEPS, "loss_first": round(hist[0], 4),
+                 "loss_last": round(hist[-1], 4), "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def batch_job_options(mix, d, net):
+    if mix == "df":
+        return dict(precision=5)
+    if mix == "stated" and d == BATCH_LATTICES[0]:
+        return dict(precision=0, net=net)
+    return dict(precision=2)
 
 
 def batch_workload(args):
-    """Time for 24 independent solves launched as one CUDA graph (device-side iteration control),
-    against the same 24 solves run one after another with host-side control."""
+    """Time for 24 independent solves launched as one CUDA graph (device-side iteration control,
+    fallback and restarts), against the same 24 solves run one after another with host-side
+    control."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -367,14 +404,15 @@ def batch_workload(args):
     import paper_0907_3261_gb300 as wd
     from paper_0907_3261_gb300 import inputs as I
     dev = torch.device("cuda", 0)
-    j = 8
-    prec = BATCH_PRECISION
+    mix = args.batch_mix
+    net, training = (train_batch_network(wd, I, torch, dev) if mix == "stated" else (None, None))
     links = {d: torch.from_numpy(I.random_links(d, LINK_EPS, seed=0)).to(dev) for d in BATCH_LATTICES}
     jobs = []
     for n, (d, L, kappa) in enumerate(batch_jobs()):
         ctx = wd.wd_create(links[d], d, kappa, CSW)
         B = torch.from_numpy(I.z4_noise(d, L, seed=100 + n)).to(dev)
-        jobs.append(dict(ctx=ctx, B=B, X=torch.zeros_like(B), j=j, precision=prec, tol=TOL))
+        jobs.append(dict(ctx=ctx, B=B, X=torch.zeros_like(B), j=BATCH_J, tol=TOL,
+                         **batch_job_options(mix, d, net)))
     del links
     site_rhs = sum(int(np.prod(d)) * L for d, L, _ in batch_jobs())
 
@@ -392,7 +430,8 @@ def batch_workload(args):
         infos = []
         for jb in jobs:
             jb["X"].zero_()
-            infos.append(wd.bbicggr_solve(jb["ctx"], jb["B"], jb["X"], j=j, tol=TOL, precision=prec)[1])
+            kw = {k: jb[k] for k in ("j", "tol", "precision", "net") if k in jb}
+            infos.append(wd.bbicggr_solve(jb["ctx"], jb["B"], jb["X"], **kw)[1])
         torch.cuda.synchronize()
         return time.perf_counter() - t0, infos
 
@@ -404,20 +443,29 @@ def batch_workload(args):
     s_s = statistics.mean(t for t, _ in ts)
     infos = tg[-1][1]
     ok = all(i["status"] == wd.WD_OK for i in infos)
+    same = all(a["iters"] == b["iters"] and a["fallbacks"] == b["fallbacks"]
+               for a, b in zip(infos, ts[-1][1]))
     out = {"metric": "time for 24 independent solves (one CUDA graph)", "value": round(g_s, 4),
            "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(g_s * 1e3, 2), "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64+f32+df32x2", "data": "synthetic",
            "config": {"workload": "batch24: lattices 8^4, 12^3x24, 16^3x32, 32^3x64 x L in {1,3,7,12} "
-                                  "(+ 8^4 and 12^3x24 again), kappa 0.115..0.124, Jacobi j=8 in FP32 "
-                                  "with the direction recurrences in double-float, true resid <= 1e-12",
-                      "precision": prec,
+                                  "(+ 8^4 and 12^3x24 again), kappa 0.115..0.124, true resid <= 1e-12",
+                      "mix": mix, "preconditioners": BATCH_MIXES[mix],
                       "jobs": len(jobs), "site_rhs_total": site_rhs},
            "sequential_host_controlled_s": round(s_s, 4),
            "speedup_vs_sequential": round(s_s / g_s, 3),
            "solves": {"status": "ok" if ok else "FAILED",
-                      "iters": [i["iters"] for i in infos],
+                      "same_as_sequential": same,
+                      "jobs": [{"dims": "x".join(map(str, d)), "L": L, "kappa": round(kappa, 5),
+                                "precond": "network" if jb.get("net") is not None else
+                                           f"jacobi p{jb['precision']}",
+                                "iters": i["iters"], "fallbacks": i["fallbacks"],
+                                "true_resid": float(f"{i['max_true_resid']:.3e}")}
+                               for (d, L, kappa), jb, i in zip(batch_jobs(), jobs, infos)],
                       "max_true_resid": max(i["max_true_resid"] for i in infos)}}
+    if training:
+        out["network_training"] = training
     print(json.dumps(out), flush=True)
     return 0 if ok else 1
 
@@ -467,6 +515,8 @@ def main():
     ap.add_argument("--no-other-form", action="store_true",
                     help="skip timing the other precision forms on the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-mix", default="stated", choices=list(BATCH_MIXES),
+                    help="preconditioners of the batch24 workload")
     ap.add_argument("--workload", default="tts", choices=["tts", "batch24"],
                     help="tts: the time-to-solution line; batch24: 24 solves in one CUDA graph")
     args = ap.parse_args()

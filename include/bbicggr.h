@@ -189,20 +189,21 @@ typedef struct {
   int L;
   int j;
   double tol;
-  bbicggr_opts opts;      /* maxit, div_thresh, precision, stall_window, net, history are used;
-                             max_restarts is not (see below) */
+  bbicggr_opts opts;      /* every option is used, as in bbicggr_solve */
   bbicggr_info info;      /* filled on return; rec_resid / true_resid may point to host arrays */
 } bbicggr_job;
 
-/* Preconditioned block BiCGGR for several independent systems at once, with the iteration
- * controlled on the device: all jobs are branches of one CUDA graph in which each solve's outer
- * iteration is a conditional while-node (the convergence test of the algorithm box runs in a
- * kernel that sets the loop condition), so the host launches once and synchronises once.
- * Differences from bbicggr_solve: no true-residual restarts and no precision fallback -- a job
- * whose recursive residual converged but whose true residual is above tol, or whose FP32 / network
- * preconditioner stalled, reports WD_NOT_CONVERGED (solve it again with bbicggr_solve from X).
- * info.mvm_actual is -1.  Returns WD_OK if every job converged, else the first job's non-OK
- * status; argument and CUDA errors return before any work. */
+/* Preconditioned block BiCGGR for several independent systems at once, with all control on the
+ * device: every job is a branch of one CUDA graph.  A job's outer iteration is a conditional
+ * while-node whose convergence test (the algorithm box's) runs in a kernel that sets the loop
+ * condition; around it a second while-node runs one solve per pass and decides after each pass,
+ * in a kernel, what bbicggr_solve decides on the host: start over from X_0 with the FP64 Jacobi
+ * preconditioner when a low-precision or network run stalled, broke down or diverged (precision
+ * fallback, opts.stall_window > 0), restart from X when the true residual is above tol (at most
+ * opts.max_restarts times), or stop.  The host launches once and synchronises once.  Each job
+ * reproduces bbicggr_solve on its own: the same iterations, restarts, fallbacks, residual
+ * history and X.  info.mvm_actual is -1.  Returns WD_OK if every job converged, else the first
+ * job's non-OK status; argument and CUDA errors return before any work. */
 int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream);
 
 void bbicggr_default_opts(bbicggr_opts* opts);

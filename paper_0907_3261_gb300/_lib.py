@@ -532,8 +532,8 @@ def bbicggr_solve_batch(jobs, stream=None):
     """Solve several independent systems in one CUDA graph with device-side iteration control.
 
     ``jobs``: list of dicts with keys ctx, B, X (device torch tensors; X holds X_0), and optional
-    j (12), tol (1e-12), maxit, div_thresh, precision, stall_window, net, history.  Returns the list
-    of info dicts (same keys as bbicggr_solve's, without restarts/fallbacks semantics)."""
+    j (12), tol (1e-12), maxit, div_thresh, max_restarts, precision, stall_window, net, history.
+    Returns the list of info dicts (the keys of bbicggr_solve's; mvm_actual is not counted)."""
     n = len(jobs)
     arr = (Job * n)()
     keep = []
@@ -546,6 +546,7 @@ def bbicggr_solve_batch(jobs, stream=None):
         o.div_thresh = float(jb.get("div_thresh", 1e2))
         o.precision = int(jb.get("precision", 0))
         o.stall_window = int(jb.get("stall_window", 16))
+        o.max_restarts = int(jb.get("max_restarts", 3))
         if jb.get("net") is not None:
             o.net = jb["net"].handle
         hist = (C.c_double * max(int(jb.get("history", 0)), 1))()
@@ -572,7 +573,8 @@ def bbicggr_solve_batch(jobs, stream=None):
         info = arr[i].info
         hist, rec, tru = keep[i][2], keep[i][3], keep[i][4]
         out.append(dict(status=info.status, status_name=lib().wd_strerror(info.status).decode(),
-                        iters=info.iters, mvm_paper=info.mvm_paper,
+                        iters=info.iters, restarts=info.restarts, fallbacks=info.fallbacks,
+                        mvm_paper=info.mvm_paper,
                         max_rec_resid=info.max_rec_resid, max_true_resid=info.max_true_resid,
                         rec_resid=np.array(rec[:]), true_resid=np.array(tru[:]),
                         history=np.array(hist[:info.history_count]), seconds=info.seconds))

@@ -1189,16 +1189,25 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
 }  // extern "C"
 
 // ================================================================== device-controlled solves
-// bbicggr_solve_batch: every job's solve becomes one branch of a single CUDA graph.  The outer
-// iteration is a conditional WHILE node whose body runs the iteration up to the R update and a
-// check kernel; the check kernel counts k, records the residual, decides (converged, diverged,
-// stalled, maxit, breakdown) and sets both the loop condition and the condition of an IF node that
-// holds the rest of the iteration (F = MR, W = AF, gamma, P, V).  The host launches the graph once
-// and synchronises once for all jobs.
+// bbicggr_solve_batch: every job's solve becomes one branch of a single CUDA graph, with the whole
+// control flow of bbicggr_solve on the device:
+//   WHILE (phase)                                   one run of block BiCGGR per pass
+//     IF (mode 0) run with the job's preconditioner
+//     IF (mode 1) run with the FP64 Jacobi preconditioner (after a fallback; X restored to X_0)
+//     true residual; phase check: fall back, restart from X, or stop
+//   run = R_0, F_0, W_0 ... ; WHILE (iterate) { alpha, U, G, Y, X, R, check; IF (continue) { F, W,
+//         gamma, P, V } }
+// The check kernels count k, record the residual, decide (converged, diverged, stalled, maxit,
+// breakdown) and set the conditions.  The host launches the graph once and synchronises once for
+// all jobs; every wait is a graph dependency, none is a spin.
 namespace {
 
+constexpr int GRAPH_STALLED = 100;   // run status: the low-precision preconditioner stopped improving
+
 struct GraphCtl {
-  int k, maxit, stall, k_best, status, L, hist_len, pad;
+  int k, maxit_run, stall, k_best, status, L, hist_len, hist_n;
+  int mode, may_fall_back, restore, iters, restarts, max_restarts, fallbacks, stall_window, maxit;
+  int runs[2], iters_mode[2];
   double tol, div, best;
   double bnorm2[WD_LMAX];
   double rec[WD_LMAX];
@@ -1215,18 +1224,43 @@ __device__ double graph_max_rel(const double* n2, GraphCtl* g) {
   return m;
 }
 
+__device__ void graph_record(GraphCtl* g, double* hist, double m) {
+  if (hist && g->hist_n < g->hist_len) hist[g->hist_n] = m;
+  if (g->hist_n < g->hist_len) g->hist_n += 1;
+}
+
+// Start of a pass: open the branch of the current mode.
+__global__ void graph_phase_begin(const GraphCtl* g, cudaGraphConditionalHandle hrun0,
+                                  cudaGraphConditionalHandle hrun1, int two_modes) {
+  if (threadIdx.x != 0) return;
+  cudaGraphSetConditional(hrun0, g->mode == 0 ? 1u : 0u);
+  if (two_modes) cudaGraphSetConditional(hrun1, g->mode == 1 ? 1u : 0u);
+}
+
+// X = X_0 when the pass is the first one after a fallback.
+__global__ void graph_restore_x(const GraphCtl* g, double2* X, const double2* X0, long long n) {
+  if (!g->restore) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    X[i] = X0[i];
+}
+
+// After R_0 of a run: the first residual check (k = 0).
 __global__ void graph_init_check(const SolverState* st, GraphCtl* g, double* hist,
                                  cudaGraphConditionalHandle hloop) {
   if (threadIdx.x != 0) return;
   const double m = graph_max_rel(st->rnorm2, g);
+  g->restore = 0;
   g->k = 0;
   g->best = m;
   g->k_best = 0;
-  if (hist && g->hist_len > 0) hist[0] = m;
+  g->maxit_run = g->maxit - g->iters;
+  g->stall = g->mode == 0 && g->may_fall_back ? g->stall_window : 0;
+  graph_record(g, hist, m);
   int done = 0, status = WD_OK;
   if (!isfinite(m)) { done = 1; status = WD_BREAKDOWN; }
   else if (m <= g->tol) { done = 1; status = WD_OK; }
-  else if (g->maxit <= 0) { done = 1; status = WD_NOT_CONVERGED; }
+  else if (g->maxit_run <= 0) { done = 1; status = WD_NOT_CONVERGED; }
   g->status = status;
   cudaGraphSetConditional(hloop, done ? 0u : 1u);
 }
@@ -1241,21 +1275,50 @@ __global__ void graph_iter_check(const SolverState* st, GraphCtl* g, double* his
   } else {
     g->k += 1;
     const double m = graph_max_rel(st->rnorm2, g);
-    if (hist && g->k < g->hist_len) hist[g->k] = m;
+    graph_record(g, hist, m);
     if (!isfinite(m)) { done = 1; status = WD_BREAKDOWN; }
     else if (m <= g->tol) { done = 1; status = WD_OK; }
     else if (m > g->div) { done = 1; status = WD_DIVERGED; }
     else {
       if (m < g->best) { g->best = m; g->k_best = g->k; }
-      if ((g->stall > 0 && g->k - g->k_best >= g->stall) || g->k >= g->maxit) {
-        done = 1;
-        status = WD_NOT_CONVERGED;
-      }
+      if (g->stall > 0 && g->k - g->k_best >= g->stall) { done = 1; status = GRAPH_STALLED; }
+      else if (g->k >= g->maxit_run) { done = 1; status = WD_NOT_CONVERGED; }
     }
   }
   g->status = status;
   cudaGraphSetConditional(hloop, done ? 0u : 1u);
   cudaGraphSetConditional(htail, done ? 0u : 1u);
+}
+
+// End of a pass, after the true residual ||b_i - A x_i||^2 is in true2: fall back to the FP64
+// preconditioner from X_0 (a stalled, broken-down or diverged low-precision run), restart from X
+// (converged recursively but not truly), or stop -- the decisions of bbicggr_solve.
+__global__ void graph_phase_end(GraphCtl* g, cudaGraphConditionalHandle hphase) {
+  if (threadIdx.x != 0) return;
+  g->iters += g->k;
+  g->runs[g->mode] += 1;
+  g->iters_mode[g->mode] += g->k;
+  int status = g->status, again = 0;
+  if (g->mode == 0 && g->may_fall_back && g->iters < g->maxit &&
+      (status == GRAPH_STALLED || status == WD_BREAKDOWN || status == WD_DIVERGED)) {
+    g->mode = 1;
+    g->restore = 1;
+    g->fallbacks += 1;
+    again = 1;
+  } else {
+    if (status == GRAPH_STALLED) status = WD_NOT_CONVERGED;
+    double mtrue = 0.0;
+    for (int i = 0; i < g->L; ++i) {
+      const double r = sqrt(g->true2[i]) / sqrt(g->bnorm2[i]);
+      if (!(r <= mtrue)) mtrue = r;
+    }
+    if (status == WD_OK && !(mtrue <= g->tol)) {
+      if (g->restarts >= g->max_restarts || g->iters >= g->maxit) status = WD_NOT_CONVERGED;
+      else { g->restarts += 1; again = 1; }
+    }
+    g->status = status;
+  }
+  cudaGraphSetConditional(hphase, again ? 1u : 0u);
 }
 
 // Enqueue `fn` on the context's capture stream as nodes of graph `g` after `deps`; the leaf nodes
@@ -1294,14 +1357,16 @@ int precondition_into(wd_ctx* c, const double* R, double* out, double* tmp, int 
 struct JobPtrs {
   const double* B;
   double* X;
+  double* X0;             // X_0, kept for a fallback (null when the job cannot fall back)
   int L, j, mode;
   bool df;
   double tol;
 };
 
-int build_job(wd_ctx* c, const JobPtrs& jp, cudaGraph_t G) {
+// One run of block BiCGGR from the current X with preconditioner `mode` into graph `RB`.
+int build_run(wd_ctx* c, const JobPtrs& jp, int mode, bool df, bool restore, cudaGraph_t RB) {
   const Op& op = c->op;
-  const int L = jp.L, j = jp.j, mode = jp.mode;
+  const int L = jp.L, j = jp.j;
   const long long rows = (long long)op.g.V * 12;
   const size_t bytes = block_bytes(c, L);
   double* R = c->blk[B_R].d();
@@ -1320,12 +1385,16 @@ int build_job(wd_ctx* c, const JobPtrs& jp, cudaGraph_t G) {
   double* hist = c->ghist;
 
   cudaGraphConditionalHandle hloop;
-  CU(cudaGraphConditionalHandleCreate(&hloop, G, 1, cudaGraphCondAssignDefault));
+  CU(cudaGraphConditionalHandleCreate(&hloop, RB, 0, 0));
   std::vector<cudaGraphNode_t> pre_leaves, a_leaves, dummy;
-  // before the loop: R_0, P_0, R~_0, R~_0^H R_0, the first check, F_0, V_0 = W_0, traces, R~_0^H V_0
-  CHECK(capture_into(c, G, {}, [&](cudaStream_t s) -> int {
+  // R_0, P_0, R~_0, R~_0^H R_0, the first check, F_0, V_0 = W_0, traces, R~_0^H V_0
+  CHECK(capture_into(c, RB, {}, [&](cudaStream_t s) -> int {
+    if (restore) {
+      graph_restore_x<<<1024, 256, 0, s>>>(g, reinterpret_cast<double2*>(jp.X),
+                                           reinterpret_cast<const double2*>(jp.X0), rows * L);
+      CU(cudaGetLastError());
+    }
     CU(cudaMemsetAsync(&st->status, 0, sizeof(int), s));
-    LAUNCH(WD_K_COLNORM, 2, launch_colnorms(jp.B, L, rows, part, g->bnorm2, s));
     LAUNCH(WD_K_RESID, 1, launch_resid_f64(op, jp.X, jp.B, R, L, s));
     LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(P, R, bytes, cudaMemcpyDeviceToDevice, s));
     LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(Rt, R, bytes, cudaMemcpyDeviceToDevice, s));
@@ -1346,16 +1415,16 @@ int build_job(wd_ctx* c, const JobPtrs& jp, cudaGraph_t G) {
   wp.conditional.type = cudaGraphCondTypeWhile;
   wp.conditional.size = 1;
   cudaGraphNode_t nwhile;
-  CU(cudaGraphAddNode(&nwhile, G, pre_leaves.data(), nullptr, pre_leaves.size(), &wp));
+  CU(cudaGraphAddNode(&nwhile, RB, pre_leaves.data(), nullptr, pre_leaves.size(), &wp));
   cudaGraph_t body = wp.conditional.phGraph_out[0];
   cudaGraphConditionalHandle htail;
   CU(cudaGraphConditionalHandleCreate(&htail, body, 0, 0));
   CHECK(capture_into(c, body, {}, [&](cudaStream_t s) -> int {
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_alpha(st, L, s));
-    LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(P, V, U, L, rows, st, s, jp.df));
+    LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(P, V, U, L, rows, st, s, df));
     CHECK(precondition_into(c, U, Gk, T, L, j, mode, s));
     LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, Gk, Y, L, s));
-    LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(jp.X, F, Gk, R, W, Y, Rt, L, rows, part, st, s, jp.df));
+    LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(jp.X, F, Gk, R, W, Y, Rt, L, rows, part, st, s, df));
     graph_iter_check<<<1, 32, 0, s>>>(st, g, hist, hloop, htail);
     CU(cudaGetLastError());
     return WD_OK;
@@ -1373,13 +1442,68 @@ int build_job(wd_ctx* c, const JobPtrs& jp, cudaGraph_t G) {
     LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, F, W, L, s));
     LAUNCH(WD_K_TRACE, 2, launch_traces(W, R, L, rows, part, st, s));
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_gamma(st, L, s));
-    LAUNCH(WD_K_UPDATE_PV, 2, launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s, jp.df));
+    LAUNCH(WD_K_UPDATE_PV, 2, launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s, df));
     return WD_OK;
   }, &dummy));
-  // after the loop: the true residual
-  CHECK(capture_into(c, G, {nwhile}, [&](cudaStream_t s) -> int {
+  return WD_OK;
+}
+
+// Adds a conditional node of `type` (handle h) to `graph` after `deps`; its body is returned.
+int add_conditional(cudaGraph_t graph, const std::vector<cudaGraphNode_t>& deps,
+                    cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                    cudaGraphNode_t* node, cudaGraph_t* body) {
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  CU(cudaGraphAddNode(node, graph, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p));
+  *body = p.conditional.phGraph_out[0];
+  return WD_OK;
+}
+
+int build_job(wd_ctx* c, const JobPtrs& jp, cudaGraph_t G) {
+  const Op& op = c->op;
+  const int L = jp.L;
+  const long long rows = (long long)op.g.V * 12;
+  const size_t bytes = block_bytes(c, L);
+  double* T = c->blk[B_T].d();
+  double2* part = static_cast<double2*>(c->part.p);
+  GraphCtl* g = static_cast<GraphCtl*>(c->gctl);
+  const bool two_modes = jp.X0 != nullptr;
+
+  cudaGraphConditionalHandle hphase;
+  CU(cudaGraphConditionalHandleCreate(&hphase, G, 1, cudaGraphCondAssignDefault));
+  std::vector<cudaGraphNode_t> pre_leaves, begin_leaves, dummy;
+  CHECK(capture_into(c, G, {}, [&](cudaStream_t s) -> int {
+    LAUNCH(WD_K_COLNORM, 2, launch_colnorms(jp.B, L, rows, part, g->bnorm2, s));
+    if (two_modes)
+      LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(jp.X0, jp.X, bytes, cudaMemcpyDeviceToDevice, s));
+    return WD_OK;
+  }, &pre_leaves));
+  cudaGraphNode_t nphase, nrun0, nrun1 = nullptr;
+  cudaGraph_t pass, rb0, rb1 = nullptr;
+  CHECK(add_conditional(G, pre_leaves, hphase, cudaGraphCondTypeWhile, &nphase, &pass));
+  cudaGraphConditionalHandle hrun0, hrun1 = 0;
+  CU(cudaGraphConditionalHandleCreate(&hrun0, pass, 0, 0));
+  if (two_modes) CU(cudaGraphConditionalHandleCreate(&hrun1, pass, 0, 0));
+  CHECK(capture_into(c, pass, {}, [&](cudaStream_t s) -> int {
+    graph_phase_begin<<<1, 32, 0, s>>>(g, hrun0, hrun1, two_modes ? 1 : 0);
+    CU(cudaGetLastError());
+    return WD_OK;
+  }, &begin_leaves));
+  CHECK(add_conditional(pass, begin_leaves, hrun0, cudaGraphCondTypeIf, &nrun0, &rb0));
+  CHECK(build_run(c, jp, jp.mode, jp.df, false, rb0));
+  if (two_modes) {
+    CHECK(add_conditional(pass, {nrun0}, hrun1, cudaGraphCondTypeIf, &nrun1, &rb1));
+    CHECK(build_run(c, jp, PM_F64, false, true, rb1));
+  }
+  // the true residual of the pass, then the decision
+  CHECK(capture_into(c, pass, {two_modes ? nrun1 : nrun0}, [&](cudaStream_t s) -> int {
     LAUNCH(WD_K_RESID, 1, launch_resid_f64(op, jp.X, jp.B, T, L, s));
     LAUNCH(WD_K_COLNORM, 2, launch_colnorms(T, L, rows, part, g->true2, s));
+    graph_phase_end<<<1, 32, 0, s>>>(g, hphase);
+    CU(cudaGetLastError());
     return WD_OK;
   }, &dummy));
   return WD_OK;
@@ -1431,9 +1555,13 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
       c->ghist_len = hl;
     }
     if (!c->capture_stream) CU(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    const bool may_fall_back = mode != PM_F64 && jb.opts.stall_window > 0;
+    if (may_fall_back) CHECK(c->blk[B_X0].ensure(block_bytes(c, jb.L)));
     GraphCtl h = {};
     h.maxit = jb.opts.maxit;
-    h.stall = mode != 0 ? jb.opts.stall_window : 0;
+    h.stall_window = jb.opts.stall_window;
+    h.may_fall_back = may_fall_back ? 1 : 0;
+    h.max_restarts = jb.opts.max_restarts;
     h.L = jb.L;
     h.hist_len = hl;
     h.tol = jb.tol;
@@ -1451,8 +1579,10 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     c->prof.timing = false;                 // no event nodes in the graph
     c->active_net = jb.opts.net;
     c->net_bf16 = jb.opts.net && jb.opts.precision == 3;
-    JobPtrs jp{static_cast<const double*>(jb.B), static_cast<double*>(jb.X), jb.L, jb.j,
-               precond_mode(jb.opts), jb.opts.precision == 2 || jb.opts.precision == 5, jb.tol};
+    const int mode = precond_mode(jb.opts);
+    double* X0 = mode != PM_F64 && jb.opts.stall_window > 0 ? c->blk[B_X0].d() : nullptr;
+    JobPtrs jp{static_cast<const double*>(jb.B), static_cast<double*>(jb.X), X0, jb.L, jb.j,
+               mode, jb.opts.precision == 2 || jb.opts.precision == 5, jb.tol};
     rc = build_job(c, jp, G);
     c->prof.timing = timing;
   }
@@ -1477,7 +1607,7 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     GraphCtl h;
     CU(cudaMemcpy(&h, c->gctl, sizeof(GraphCtl), cudaMemcpyDeviceToHost));
     bbicggr_info& in = jb.info;
-    const int jeff = jb.opts.net ? 0 : jb.j;
+    const int jeff = jb.opts.net ? 0 : jb.j;    // run 0: the job's preconditioner; run 1: FP64 Jacobi
     double mtrue = 0.0, mrec = 0.0;
     double tr[WD_LMAX];
     for (int k = 0; k < jb.L; ++k) {
@@ -1488,18 +1618,19 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
     int status = h.status;
     if (status == WD_OK && !(mtrue <= jb.tol)) status = WD_NOT_CONVERGED;
     in.status = status;
-    in.iters = h.k;
-    in.restarts = 0;
-    in.fallbacks = 0;
-    in.mvm_paper = (long long)jb.L * (2LL * (jeff + 1) * h.k + 1);
+    in.iters = h.iters;
+    in.restarts = h.restarts;
+    in.fallbacks = h.fallbacks;
+    in.mvm_paper = (long long)jb.L * (2LL * (jeff + 1) * h.iters_mode[0] + h.runs[0] +
+                                      2LL * (jb.j + 1) * h.iters_mode[1] + h.runs[1]);
     in.mvm_actual = -1;
     in.max_rec_resid = mrec;
     in.max_true_resid = mtrue;
     if (in.rec_resid) std::memcpy(in.rec_resid, h.rec, jb.L * sizeof(double));
     if (in.true_resid) std::memcpy(in.true_resid, tr, jb.L * sizeof(double));
     in.history_count = 0;
-    if (jb.opts.history && h.hist_len > 0) {
-      const int n = std::min(h.k + 1, h.hist_len);
+    if (jb.opts.history && h.hist_n > 0) {
+      const int n = std::min(h.hist_n, h.hist_len);
       CU(cudaMemcpy(jb.opts.history, c->ghist, n * sizeof(double), cudaMemcpyDeviceToHost));
       in.history_count = n;
     }

@@ -1,6 +1,7 @@
 // C-ABI of the learned preconditioner network (declared in include/bbicggr.h): weights, Adam
-// state and activation workspace of one network, inference G = N(R), and one training step on
-// pairs (R, E = A^{-1} R).  The kernels live in net.cu; see its header for the network.
+// state and the activation workspaces of one network (one per context it runs on), inference
+// G = N(R), and one training step on pairs (R, E = A^{-1} R).  The kernels live in net.cu; see its
+// header for the network.
 #include <cstring>
 #include <new>
 #include <vector>
@@ -38,6 +39,33 @@ constexpr int NET_BLOCKS = 608;     // reduction blocks of the loss and weight-g
 
 }  // namespace
 
+// Activations (and, for training, the loss and gradient reductions) for one lattice volume V and
+// L.  A network keeps one workspace per context it is applied on, so that solves on different
+// contexts -- the jobs of one batch graph run at the same time -- never share buffers, and one
+// for training (key nullptr), whose calls run one after another.
+struct NetWs {
+  const void* key = nullptr;
+  bool train = false;
+  long long V = 0;
+  int L = 0;
+  std::vector<float*> act;      // act[l]: input of layer l; act[layers]: output
+  float* dA = nullptr;
+  float* dB = nullptr;
+  double* wcol = nullptr;
+  double* loss = nullptr;
+  double* lpart = nullptr;
+  double2* wpart = nullptr;
+  double* norms = nullptr;
+  void release() {
+    for (float* a : act) cudaFree(a);
+    act.clear();
+    cudaFree(dA); cudaFree(dB); cudaFree(wcol); cudaFree(loss); cudaFree(lpart); cudaFree(wpart);
+    cudaFree(norms);
+    dA = dB = nullptr; wcol = loss = lpart = norms = nullptr; wpart = nullptr;
+    V = 0; L = 0;
+  }
+};
+
 struct wd_net {
   int layers = 0, hidden = 0;
   std::vector<int> ch;          // channels: ch[0] = 1, ch[layers] = 1
@@ -49,24 +77,10 @@ struct wd_net {
   float2* m = nullptr;
   float2* v = nullptr;
   int t = 0;                    // Adam steps taken
-  // workspace for (V, L)
-  long long V = 0;
-  int L = 0;
-  std::vector<float*> act;      // act[l]: input of layer l; act[layers]: output
-  float* dA = nullptr;
-  float* dB = nullptr;
-  double* wcol = nullptr;
-  double* loss = nullptr;
-  double* lpart = nullptr;
-  double2* wpart = nullptr;
-  double* norms = nullptr;
+  std::vector<NetWs*> ws;
   void free_ws() {
-    for (float* a : act) cudaFree(a);
-    act.clear();
-    cudaFree(dA); cudaFree(dB); cudaFree(wcol); cudaFree(loss); cudaFree(lpart); cudaFree(wpart);
-    cudaFree(norms);
-    dA = dB = nullptr; wcol = loss = lpart = norms = nullptr; wpart = nullptr;
-    V = 0; L = 0;
+    for (NetWs* w : ws) { w->release(); delete w; }
+    ws.clear();
   }
 };
 
@@ -74,40 +88,62 @@ namespace {
 
 size_t chan_floats(long long V, int L) { return (size_t)12 * V * L * 2; }
 
-int net_workspace(wd_net* n, long long V, int L) {
-  if (n->V == V && n->L == L) return WD_OK;
-  n->free_ws();
-  const size_t cf = chan_floats(V, L) * sizeof(float);
-  n->act.assign(n->layers + 1, nullptr);
-  for (int l = 0; l <= n->layers; ++l) NCU(cudaMalloc(&n->act[l], cf * n->ch[l]));
-  int maxc = 1;
-  for (int c : n->ch) maxc = c > maxc ? c : maxc;
-  NCU(cudaMalloc(&n->dA, cf * maxc));
-  NCU(cudaMalloc(&n->dB, cf * maxc));
-  NCU(cudaMalloc(&n->wcol, WD_LMAX * sizeof(double)));
-  NCU(cudaMalloc(&n->loss, sizeof(double)));
-  NCU(cudaMalloc(&n->lpart, NET_BLOCKS * sizeof(double)));
-  NCU(cudaMalloc(&n->norms, (size_t)(PART_STRIDE * NET_BLOCKS + WD_LMAX) * sizeof(double2)));
-  size_t maxne = 0;
-  for (int l = 0; l < n->layers; ++l) {
-    const size_t ne = (size_t)9 * n->ch[l + 1] * n->ch[l] * 16;
-    maxne = ne > maxne ? ne : maxne;
+// The workspace of (key, train) sized for (V, L), allocated or resized here unless `s` is being
+// captured into a graph, where allocation is not allowed (wd_net_prepare runs before a capture).
+int net_workspace(wd_net* n, const void* key, bool train, long long V, int L, cudaStream_t s,
+                  NetWs** out) {
+  NetWs* w = nullptr;
+  for (NetWs* e : n->ws)
+    if (e->key == key && e->train == train) w = e;
+  if (w && w->V == V && w->L == L) { *out = w; return WD_OK; }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  NCU(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {
+    wd_set_error("network workspace not prepared for V = %lld, L = %d before the capture", V, L);
+    return WD_EINVAL;
   }
-  NCU(cudaMalloc(&n->wpart, (size_t)NET_BLOCKS * maxne * sizeof(double2)));
-  n->V = V;
-  n->L = L;
+  if (!w) {
+    w = new (std::nothrow) NetWs();
+    if (!w) { wd_set_error("host allocation failed"); return WD_ENOMEM; }
+    w->key = key;
+    w->train = train;
+    n->ws.push_back(w);
+  }
+  w->release();
+  const size_t cf = chan_floats(V, L) * sizeof(float);
+  w->act.assign(n->layers + 1, nullptr);
+  for (int l = 0; l <= n->layers; ++l) NCU(cudaMalloc(&w->act[l], cf * n->ch[l]));
+  if (train) {
+    int maxc = 1;
+    for (int c : n->ch) maxc = c > maxc ? c : maxc;
+    NCU(cudaMalloc(&w->dA, cf * maxc));
+    NCU(cudaMalloc(&w->dB, cf * maxc));
+    NCU(cudaMalloc(&w->wcol, WD_LMAX * sizeof(double)));
+    NCU(cudaMalloc(&w->loss, sizeof(double)));
+    NCU(cudaMalloc(&w->lpart, NET_BLOCKS * sizeof(double)));
+    NCU(cudaMalloc(&w->norms, (size_t)(PART_STRIDE * NET_BLOCKS + WD_LMAX) * sizeof(double2)));
+    size_t maxne = 0;
+    for (int l = 0; l < n->layers; ++l) {
+      const size_t ne = (size_t)9 * n->ch[l + 1] * n->ch[l] * 16;
+      maxne = ne > maxne ? ne : maxne;
+    }
+    NCU(cudaMalloc(&w->wpart, (size_t)NET_BLOCKS * maxne * sizeof(double2)));
+  }
+  w->V = V;
+  w->L = L;
+  *out = w;
   return WD_OK;
 }
 
 // act[layers] = N(act[0]) (activations of every layer kept); bf16: the activations are stored
 // in BF16 (the buffers, sized for FP32, hold them in their first half).
-int net_forward(const Op& op, wd_net* n, int L, cudaStream_t s, bool bf16 = false) {
+int net_forward(const Op& op, wd_net* n, NetWs* w, int L, cudaStream_t s, bool bf16 = false) {
   for (int l = 0; l < n->layers; ++l) {
     if (bf16)
-      NCU(net_launch_layer_bf16(op, n->act[l], n->act[l + 1], n->W + n->off[l], n->ch[l],
+      NCU(net_launch_layer_bf16(op, w->act[l], w->act[l + 1], n->W + n->off[l], n->ch[l],
                                 n->ch[l + 1], L, s));
     else
-      NCU(net_launch_layer(op, n->act[l], n->act[l + 1], n->W + n->off[l], n->ch[l],
+      NCU(net_launch_layer(op, w->act[l], w->act[l + 1], n->W + n->off[l], n->ch[l],
                            n->ch[l + 1], L, s));
   }
   return WD_OK;
@@ -147,19 +183,21 @@ int set_weights(wd_net* n, const void* w) {
 
 }  // namespace
 
-// Internal: allocate the network's workspace for this lattice and L (before a stream capture).
+// Internal: allocate the network's workspace for this context and L (before a stream capture).
 int wd_net_prepare(wd_ctx* ctx, wd_net* n, int L) {
-  return net_workspace(n, wd_ctx_op(ctx)->g.V, L);
+  NetWs* w;
+  return net_workspace(n, ctx, false, wd_ctx_op(ctx)->g.V, L, nullptr, &w);
 }
 
 // Internal: G = N(R) for device blocks R, G (site-major FP64), used by the solver.
 int wd_net_precondition(wd_ctx* ctx, wd_net* n, const double* R, double* G, int L, bool bf16,
                         cudaStream_t s) {
   const Op& op = *wd_ctx_op(ctx);
-  NCHECK(net_workspace(n, op.g.V, L));
-  NCU(net_launch_to_cm(R, n->act[0], op.g.V, L, bf16, s));
-  NCHECK(net_forward(op, n, L, s, bf16));
-  NCU(net_launch_from_cm(n->act[n->layers], G, op.g.V, L, bf16, s));
+  NetWs* w;
+  NCHECK(net_workspace(n, ctx, false, op.g.V, L, s, &w));
+  NCU(net_launch_to_cm(R, w->act[0], op.g.V, L, bf16, s));
+  NCHECK(net_forward(op, n, w, L, s, bf16));
+  NCU(net_launch_from_cm(w->act[n->layers], G, op.g.V, L, bf16, s));
   return WD_OK;
 }
 
@@ -245,24 +283,25 @@ int wd_net_loss_grad(wd_ctx* ctx, wd_net* n, const void* R, const void* E, int L
   const Op& op = *wd_ctx_op(ctx);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long V = op.g.V;
-  NCHECK(net_workspace(n, V, L));
+  NetWs* w;
+  NCHECK(net_workspace(n, nullptr, true, V, L, s, &w));
   // forward, keeping the activations
-  NCU(net_launch_to_cm(static_cast<const double*>(R), n->act[0], (int)V, L, false, s));
-  NCHECK(net_forward(op, n, L, s));
+  NCU(net_launch_to_cm(static_cast<const double*>(R), w->act[0], (int)V, L, false, s));
+  NCHECK(net_forward(op, n, w, L, s));
   // column weights 1 / (L ||e_i||^2), loss and delta = d loss / d conj(y)
-  double2* npart = reinterpret_cast<double2*>(n->norms);
-  double* norm2 = n->norms + 2 * (size_t)PART_STRIDE * NET_BLOCKS;
+  double2* npart = reinterpret_cast<double2*>(w->norms);
+  double* norm2 = w->norms + 2 * (size_t)PART_STRIDE * NET_BLOCKS;
   NCU(launch_colnorms(static_cast<const double*>(E), L, V * 12, npart, norm2, s));
-  wcol_kernel<<<1, 32, 0, s>>>(norm2, n->wcol, L);
+  wcol_kernel<<<1, 32, 0, s>>>(norm2, w->wcol, L);
   NCU(cudaGetLastError());
-  NCU(net_launch_loss_delta(n->act[n->layers], static_cast<const double*>(E), n->wcol, n->dA,
-                            n->lpart, NET_BLOCKS, n->loss, (int)V, L, s));
+  NCU(net_launch_loss_delta(w->act[n->layers], static_cast<const double*>(E), w->wcol, w->dA,
+                            w->lpart, NET_BLOCKS, w->loss, (int)V, L, s));
   // backward through the layers
-  float* delta = n->dA;
-  float* other = n->dB;
+  float* delta = w->dA;
+  float* other = w->dB;
   for (int l = n->layers - 1; l >= 0; --l) {
     const int cin = n->ch[l], cout = n->ch[l + 1];
-    NCU(net_launch_wgrad(op, n->act[l], delta, cin, cout, L, n->wpart, NET_BLOCKS, n->G + n->off[l], s));
+    NCU(net_launch_wgrad(op, w->act[l], delta, cin, cout, L, w->wpart, NET_BLOCKS, n->G + n->off[l], s));
     if (l > 0) {
       NCU(net_launch_adjoint_weights(n->W + n->off[l], n->Wadj + n->off[l], cin, cout, s));
       NCU(net_launch_layer(op, delta, other, n->Wadj + n->off[l], cout, cin, L, s));
@@ -272,7 +311,7 @@ int wd_net_loss_grad(wd_ctx* ctx, wd_net* n, const void* R, const void* E, int L
     }
   }
   if (loss) {
-    NCU(cudaMemcpyAsync(loss, n->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NCU(cudaMemcpyAsync(loss, w->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   }
   if (grad) {
     NCU(cudaMemcpyAsync(grad, n->G, n->nw * sizeof(double2), cudaMemcpyDefault, s));
