@@ -470,6 +470,72 @@ def batch_workload(args):
     return 0 if ok else 1
 
 
+# ---------------------------------------------------------------- the FP64 method on 8^3 x 16
+GRID_DIMS = (8, 8, 8, 16)
+GRID_L = [1, 2, 4, 8, 12]
+GRID_J = [0, 4, 8, 12, 16]
+GRID_SCAN_MAXIT = 2000
+
+
+def grid8_workload(args):
+    """The plain FP64 method on an 8^3 x 16 lattice: kappa rises from 0.115 in steps of 0.001 until
+    the L = 1, j = 0 solve first needs more than 2000 iterations; then every L in {1, 2, 4, 8, 12}
+    with every j in {0, 4, 8, 12, 16} is solved at three kappa of the scan (the first, the middle
+    and the last that converged within 2000 iterations), with its outer iterations, #MVM per
+    column, time to solution and true residual.  Times are medians of --steps solves after one
+    untimed solve."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0907_3261_gb300 as wd
+    from paper_0907_3261_gb300 import inputs as I
+    dev = torch.device("cuda", 0)
+    links = torch.from_numpy(I.random_links(GRID_DIMS, LINK_EPS, seed=0)).to(dev)
+    Bs = {L: torch.from_numpy(I.z4_noise(GRID_DIMS, L, seed=1)).to(dev) for L in GRID_L}
+    scan = []
+    kappa = 0.115
+    while True:
+        ctx = wd.wd_create(links, GRID_DIMS, kappa, CSW)
+        _, info = wd.bbicggr_solve(ctx, Bs[1], j=0, tol=TOL, maxit=GRID_SCAN_MAXIT)
+        scan.append({"kappa": round(kappa, 3), "iters": info["iters"],
+                     "status": info["status_name"]})
+        if info["status"] != wd.WD_OK or info["iters"] > GRID_SCAN_MAXIT or kappa > 0.2:
+            break
+        kappa += 0.001
+    ok_kappas = [r["kappa"] for r in scan if r["status"] == "WD_OK"]
+    picks = sorted({ok_kappas[0], ok_kappas[len(ok_kappas) // 2], ok_kappas[-1]})
+    rows = []
+    for kappa in picks:
+        ctx = wd.wd_create(links, GRID_DIMS, kappa, CSW)
+        for L in GRID_L:
+            for j in GRID_J:
+                X = torch.zeros_like(Bs[L])
+                wd.bbicggr_solve(ctx, Bs[L], X, j=j, tol=TOL, maxit=20000)
+                times = []
+                for _ in range(args.steps):
+                    X.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, info = wd.bbicggr_solve(ctx, Bs[L], X, j=j, tol=TOL, maxit=20000)
+                    torch.cuda.synchronize()
+                    times.append(time.perf_counter() - t0)
+                rows.append({"kappa": kappa, "L": L, "j": j, "status": info["status_name"],
+                             "iters": info["iters"], "mvm_per_col": info["mvm_paper"] // L,
+                             "tts_s": round(statistics.median(times), 5),
+                             "true_resid": float(f"{info['max_true_resid']:.3e}")})
+    ok = all(r["status"] == "WD_OK" for r in rows)
+    out = {"metric": "time-to-solution grid, plain FP64 method, 8^3x16", "unit": "s",
+           "n_gpus": 1, "steps": args.steps, "dtype": "f64", "data": "synthetic",
+           "higher_is_better": False,
+           "config": {"workload": "8^3x16, links SU3proj(1+0.2G) seed 0, c_SW 1.0, Z4 sources "
+                                  "seed 1, tol 1e-12, L in {1,2,4,8,12} x j in {0,4,8,12,16}"},
+           "kappa_scan": scan, "kappa_picked": picks, "grid": rows,
+           "status": "ok" if ok else "FAILED"}
+    print(json.dumps(out), flush=True)
+    return 0 if ok else 1
+
+
 def gpu_small_solves(wd, I, dev, prec):
     """The same c1 and c2 solves on the GPU (default form), for the side-by-side baseline."""
     import torch
@@ -517,8 +583,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-mix", default="stated", choices=list(BATCH_MIXES),
                     help="preconditioners of the batch24 workload")
-    ap.add_argument("--workload", default="tts", choices=["tts", "batch24"],
-                    help="tts: the time-to-solution line; batch24: 24 solves in one CUDA graph")
+    ap.add_argument("--workload", default="tts", choices=["tts", "batch24", "grid8"],
+                    help="tts: the time-to-solution line; batch24: 24 solves in one CUDA graph; "
+                         "grid8: the FP64 method's kappa scan and L x j grid on 8^3x16")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -526,6 +593,8 @@ def main():
         return reference_arm(args)
     if args.workload == "batch24":
         return batch_workload(args)
+    if args.workload == "grid8":
+        return grid8_workload(args)
 
     import numpy as np
     import torch
