@@ -296,6 +296,19 @@ int wd_set_tile(wd_ctx* ctx, int L, int precision, int rhs_per_thread, int block
 int wd_link_reals(const wd_ctx* ctx, int* reals);
 int wd_set_link_reals(wd_ctx* ctx, int reals);
 
+/* Form of the FP64 stencil Y = A X, R = B - A X and of the FP64 Jacobi sweep (Eq. (1), Sec. 2),
+ * which carry the outer method's products W = AF, Y = AG, the true residual and precision 0's
+ * preconditioner.  1 (the default for links whose rows and columns have norm <= 1 + 1e-6, so
+ * unitary links): the hopping sums run on the FP32 lanes, every operand cut exactly into three
+ * FP32 numbers and the products summed exactly on fixed grids, so that the hopping term is
+ * exact to ~2^-52 of its bound before one FP64 rounding; the site blocks, the spin projection
+ * and the final combination stay FP64.  It is as accurate as FP64 arithmetic and about twice as
+ * fast on GB300, whose FP64 pipe issues two lanes per clock per SM.  0: every operation on the
+ * FP64 pipe.  Asking for 1 with other links is WD_EINVAL.  wd_get_apply_form returns the form
+ * (-1 for a NULL ctx). */
+int wd_set_apply_form(wd_ctx* ctx, int form);
+int wd_get_apply_form(const wd_ctx* ctx);
+
 /* ---- Domain decomposition across ranks (the paper picks the Jacobi preconditioner for its
  * parallelism, Sec. 2).  The lattice is cut into slabs along t; a rank's context is created with
  * wd_create on its slab extended by one t-slice on each side (dims {Lx, Ly, Lz, T + 2}, T >= 1

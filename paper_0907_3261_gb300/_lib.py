@@ -120,6 +120,10 @@ def lib():
     L.wd_link_reals.restype = C.c_int
     L.wd_set_link_reals.argtypes = [vp, i]
     L.wd_set_link_reals.restype = C.c_int
+    L.wd_set_apply_form.argtypes = [vp, i]
+    L.wd_set_apply_form.restype = C.c_int
+    L.wd_get_apply_form.argtypes = [vp]
+    L.wd_get_apply_form.restype = C.c_int
     L.bb_update_u.argtypes = [vp, vp, vp, vp, i, vp, vp, i, vp]
     L.bb_update_xr.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i, vp, vp, vp, i, vp]
     L.bb_update_pv.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i, vp, vp, i, vp]
@@ -433,6 +437,15 @@ def wd_link_reals(ctx: Context) -> int:
 def wd_set_link_reals(ctx: Context, reals: int) -> None:
     """Choose the link format of the low-precision sweeps (12 needs special unitary links)."""
     _check(lib().wd_set_link_reals(ctx.handle, int(reals)))
+
+
+def wd_set_apply_form(ctx: Context, form: int) -> None:
+    """Form of the FP64 stencils: 1 = hopping sums exact on the FP32 lanes (unitary links), 0 = FP64 pipe."""
+    _check(lib().wd_set_apply_form(ctx.handle, int(form)))
+
+
+def wd_get_apply_form(ctx: Context) -> int:
+    return int(lib().wd_get_apply_form(ctx.handle))
 
 
 # ---------------------------------------------------------------- learned preconditioner

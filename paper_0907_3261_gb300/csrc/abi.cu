@@ -501,7 +501,7 @@ int precondition(wd_ctx* c, const double* R, double* a, double* b, double** res,
   double* nxt = b;
   for (int i = 1; i < j; ++i) {
     CHECK(halo_exchange(c, cur, L, s));
-    LAUNCH(WD_K_JACOBI, 1, launch_jacobi_f64(op, cur, R, nxt, L, s));
+    LAUNCH(WD_K_JACOBI, stencil_kernels(op), launch_jacobi_f64(op, cur, R, nxt, L, s));
     if (hop_count) ++*hop_count;
     double* t = cur;
     cur = nxt;
@@ -564,7 +564,7 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
 
   // R_0 = B - A X_0;  P_0 = R_0;  R~_0 = R_0
   CHECK(halo_exchange(c, X, L, s));
-  LAUNCH(WD_K_RESID, 1, launch_resid_f64(op, X, B, R, L, s));
+  LAUNCH(WD_K_RESID, stencil_kernels(op), launch_resid_f64(op, X, B, R, L, s));
   ++*hop_count;
   LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(P, R, bytes, cudaMemcpyDeviceToDevice, s));
   LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(Rt, R, bytes, cudaMemcpyDeviceToDevice, s));
@@ -583,7 +583,7 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
   CHECK(precondition(c, R, pF, pT, &res, L, j, precision, hop_count, s));
   if (res != pF) { pT = pF; pF = res; }
   CHECK(halo_exchange(c, pF, L, s));
-  LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pF, W, L, s));
+  LAUNCH(WD_K_APPLY, stencil_kernels(op), launch_apply_f64(op, pF, W, L, s));
   ++*hop_count;
   LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(V, W, bytes, cudaMemcpyDeviceToDevice, s));
   LAUNCH(WD_K_TRACE, 2, launch_traces(in(W), in(R), L, rows, part, st, s));
@@ -602,7 +602,7 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
     CHECK(precondition(c, U, pG, pT, &res, L, j, precision, hop_count, s));   // G_k = M U_k
     if (res != pG) { pT = pG; pG = res; }
     CHECK(halo_exchange(c, pG, L, s));
-    LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pG, Y, L, s));                  // Y_k = A G_k
+    LAUNCH(WD_K_APPLY, stencil_kernels(op), launch_apply_f64(op, pG, Y, L, s));                  // Y_k = A G_k
     ++*hop_count;
     LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(in(X), cin(pF), cin(pG), in(R), cin(W), cin(Y), cin(Rt), L, rows, part, st, s, df));   // X_{k+1}, R_{k+1}
     CHECK(dom_sum(c, st->rtr_new, 2 * L * L, s));
@@ -620,7 +620,7 @@ int run_bbicggr(wd_ctx* c, const double* B, double* X, int L, int j, int precisi
     CHECK(precondition(c, R, pF, pT, &res, L, j, precision, hop_count, s));   // F_{k+1} = M R_{k+1}
     if (res != pF) { pT = pF; pF = res; }
     CHECK(halo_exchange(c, pF, L, s));
-    LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, pF, W, L, s));                  // W_{k+1} = A F_{k+1}
+    LAUNCH(WD_K_APPLY, stencil_kernels(op), launch_apply_f64(op, pF, W, L, s));                  // W_{k+1} = A F_{k+1}
     ++*hop_count;
     LAUNCH(WD_K_TRACE, 2, launch_traces(in(W), in(R), L, rows, part, st, s));  // Tr[W^H R], Tr[W^H W]
     CHECK(dom_sum(c, &st->trwr, 3, s));
@@ -687,6 +687,8 @@ void wd_destroy(wd_ctx* c) {
   cudaFree(c->op.links32);
   cudaFree(c->op.clov_inv32);
   cudaFree(c->op.clov_bound32);
+  cudaFree(c->op.links_x3);
+  cudaFree(c->op.xexp);
   for (auto& b : c->blk) b.release();
   for (auto& b : c->blk32) b.release();
   c->part.release();
@@ -731,6 +733,13 @@ static int create_impl(wd_ctx* c, const void* links, const int dims[4], cudaStre
   if (h[0]) {
     set_err("a 6x6 clover block A_D is singular for kappa=%g c_SW=%g", op.kappa, op.csw);
     return WD_BREAKDOWN;
+  }
+  if (op.links_unitary) {   // the FP32-lane form of the FP64 stencil (its bounds need unitary links)
+    CU(cudaMalloc(&op.links_x3, V * 4 * 27 * sizeof(float4)));
+    CU(cudaMalloc(&op.xexp, V * WD_LMAX * sizeof(int)));
+    CU(launch_link_split(op, s));
+    CU(cudaStreamSynchronize(s));
+    op.apply_form = 1;
   }
   return WD_OK;
 }
@@ -879,6 +888,19 @@ int wd_set_link_reals(wd_ctx* c, int reals) {
   return WD_OK;
 }
 
+int wd_set_apply_form(wd_ctx* c, int form) {
+  if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
+  if (form != 0 && form != 1) { set_err("stencil form %d not in {0, 1}", form); return WD_EINVAL; }
+  if (form == 1 && !c->op.links_x3) {
+    set_err("the FP32-lane stencil needs links whose rows and columns have norm <= 1 + %g", LINK12_TOL);
+    return WD_EINVAL;
+  }
+  c->op.apply_form = form;
+  return WD_OK;
+}
+
+int wd_get_apply_form(const wd_ctx* c) { return c ? c->op.apply_form : -1; }
+
 int wd_set_domain(wd_ctx* c, const wd_domain* dom) {
   if (!c) { set_err("ctx is NULL"); return WD_EINVAL; }
   if (!dom) { c->dom_on = false; return WD_OK; }
@@ -921,7 +943,7 @@ int wd_apply(wd_ctx* c, const void* X, void* Y, int L, void* stream) {
     xd = c->stage_in.d();
     CHECK(halo_exchange(c, c->stage_in.d(), L, s));
   }
-  LAUNCH(WD_K_APPLY, 1, launch_apply_f64(c->op, xd, yd, L, s));
+  LAUNCH(WD_K_APPLY, stencil_kernels(c->op), launch_apply_f64(c->op, xd, yd, L, s));
   if (!y_dev) CU(cudaMemcpyAsync(Y, yd, bytes, cudaMemcpyDeviceToHost, s));
   if (staged_x || !y_dev) CU(cudaStreamSynchronize(s));
   harvest(c);
@@ -1145,7 +1167,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     // true residual ||b_i - A x_i|| / ||b_i||
     double* T = c->blk[B_T].d();
     CHECK(halo_exchange(c, Xd, L, s));
-    LAUNCH(WD_K_RESID, 1, launch_resid_f64(c->op, Xd, Bd, T, L, s));
+    LAUNCH(WD_K_RESID, stencil_kernels(c->op), launch_resid_f64(c->op, Xd, Bd, T, L, s));
     ++hops;
     double t2[WD_LMAX];
     LAUNCH(WD_K_COLNORM, 2, launch_colnorms(T + off, L, rows, static_cast<double2*>(c->part.p), c->bnorm2_dev + WD_LMAX, s));
@@ -1395,14 +1417,14 @@ int build_run(wd_ctx* c, const JobPtrs& jp, int mode, bool df, bool restore, cud
       CU(cudaGetLastError());
     }
     CU(cudaMemsetAsync(&st->status, 0, sizeof(int), s));
-    LAUNCH(WD_K_RESID, 1, launch_resid_f64(op, jp.X, jp.B, R, L, s));
+    LAUNCH(WD_K_RESID, stencil_kernels(op), launch_resid_f64(op, jp.X, jp.B, R, L, s));
     LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(P, R, bytes, cudaMemcpyDeviceToDevice, s));
     LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(Rt, R, bytes, cudaMemcpyDeviceToDevice, s));
     LAUNCH(WD_K_GRAM, 2, launch_gram(Rt, R, L, rows, part, st, GRAM_RTR, true, s));
     graph_init_check<<<1, 32, 0, s>>>(st, g, hist, hloop);
     CU(cudaGetLastError());
     CHECK(precondition_into(c, R, F, T, L, j, mode, s));
-    LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, F, W, L, s));
+    LAUNCH(WD_K_APPLY, stencil_kernels(op), launch_apply_f64(op, F, W, L, s));
     LAUNCH(WD_K_COPY, 0, cudaMemcpyAsync(V, W, bytes, cudaMemcpyDeviceToDevice, s));
     LAUNCH(WD_K_TRACE, 2, launch_traces(W, R, L, rows, part, st, s));
     LAUNCH(WD_K_GRAM, 2, launch_gram(Rt, V, L, rows, part, st, GRAM_RTV, false, s));
@@ -1423,7 +1445,7 @@ int build_run(wd_ctx* c, const JobPtrs& jp, int mode, bool df, bool restore, cud
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_alpha(st, L, s));
     LAUNCH(WD_K_UPDATE_U, 1, launch_update_u(P, V, U, L, rows, st, s, df));
     CHECK(precondition_into(c, U, Gk, T, L, j, mode, s));
-    LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, Gk, Y, L, s));
+    LAUNCH(WD_K_APPLY, stencil_kernels(op), launch_apply_f64(op, Gk, Y, L, s));
     LAUNCH(WD_K_UPDATE_XR, 2, launch_update_xr(jp.X, F, Gk, R, W, Y, Rt, L, rows, part, st, s, df));
     graph_iter_check<<<1, 32, 0, s>>>(st, g, hist, hloop, htail);
     CU(cudaGetLastError());
@@ -1439,7 +1461,7 @@ int build_run(wd_ctx* c, const JobPtrs& jp, int mode, bool df, bool restore, cud
   cudaGraph_t tail = ip.conditional.phGraph_out[0];
   CHECK(capture_into(c, tail, {}, [&](cudaStream_t s) -> int {
     CHECK(precondition_into(c, R, F, T, L, j, mode, s));
-    LAUNCH(WD_K_APPLY, 1, launch_apply_f64(op, F, W, L, s));
+    LAUNCH(WD_K_APPLY, stencil_kernels(op), launch_apply_f64(op, F, W, L, s));
     LAUNCH(WD_K_TRACE, 2, launch_traces(W, R, L, rows, part, st, s));
     LAUNCH(WD_K_SOLVE_LL, 1, launch_solve_gamma(st, L, s));
     LAUNCH(WD_K_UPDATE_PV, 2, launch_update_pv(P, V, R, W, U, Y, Rt, L, rows, part, st, s, df));
@@ -1500,7 +1522,7 @@ int build_job(wd_ctx* c, const JobPtrs& jp, cudaGraph_t G) {
   }
   // the true residual of the pass, then the decision
   CHECK(capture_into(c, pass, {two_modes ? nrun1 : nrun0}, [&](cudaStream_t s) -> int {
-    LAUNCH(WD_K_RESID, 1, launch_resid_f64(op, jp.X, jp.B, T, L, s));
+    LAUNCH(WD_K_RESID, stencil_kernels(op), launch_resid_f64(op, jp.X, jp.B, T, L, s));
     LAUNCH(WD_K_COLNORM, 2, launch_colnorms(T, L, rows, part, g->true2, s));
     graph_phase_end<<<1, 32, 0, s>>>(g, hphase);
     CU(cudaGetLastError());

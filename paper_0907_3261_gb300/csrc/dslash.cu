@@ -205,7 +205,9 @@ inline unsigned grid_for(long long n) { return (unsigned)((n + DS_THREADS - 1) /
 }  // namespace
 
 // ------------------------------------------------------------------ launchers (FP64)
+// With op.apply_form 1 the stencils run in their FP32-lane form (dslash_x3.cu).
 cudaError_t launch_apply_f64(const Op& op, const double* x, double* y, int L, cudaStream_t st) {
+  if (op.apply_form == 1) return launch_apply_x3(op, x, y, L, st);
   dslash_kernel<double, double, double, double, MODE_APPLY>
       <<<grid_for((long long)op.g.V * L), DS_THREADS, 0, st>>>(x, y, nullptr, op.links, op.clov,
                                                                op.g, L, op.kappa);
@@ -214,6 +216,7 @@ cudaError_t launch_apply_f64(const Op& op, const double* x, double* y, int L, cu
 
 cudaError_t launch_resid_f64(const Op& op, const double* x, const double* b, double* y, int L,
                              cudaStream_t st) {
+  if (op.apply_form == 1) return launch_resid_x3(op, x, b, y, L, st);
   dslash_kernel<double, double, double, double, MODE_RESID>
       <<<grid_for((long long)op.g.V * L), DS_THREADS, 0, st>>>(x, y, b, op.links, op.clov, op.g,
                                                                L, op.kappa);
@@ -222,6 +225,7 @@ cudaError_t launch_resid_f64(const Op& op, const double* x, const double* b, dou
 
 cudaError_t launch_jacobi_f64(const Op& op, const double* g_in, const double* u, double* g_out,
                               int L, cudaStream_t st) {
+  if (op.apply_form == 1) return launch_jacobi_x3(op, g_in, u, g_out, L, st);
   dslash_kernel<double, double, double, double, MODE_JACOBI>
       <<<grid_for((long long)op.g.V * L), DS_THREADS, 0, st>>>(g_in, g_out, u, op.links,
                                                                op.clov_inv, op.g, L, op.kappa);

@@ -29,6 +29,12 @@ struct Op {
   // max(sum_j |Re D_ij|, sum_j |Im D_ij|), rounded up -- a bound on the partial sums of a row
   // times a vector in units of the vector's largest real part.
   float* clov_bound32;
+  // The FP32-lane form of the FP64 stencil (dslash_x3.cu): the links cut into three FP32 levels,
+  // [site][mu][level][entry] as (re, re, im, im) (null when the links are not unitary), a scratch
+  // of V * WD_LMAX exponents, and the form in use (1: this one, 0: the FP64-pipe kernel).
+  float4* links_x3;
+  int* xexp;
+  int apply_form;
 };
 
 // Largest entry error |row2 - conj(row0 x row1)| of a link that still counts as special unitary.
@@ -42,6 +48,16 @@ cudaError_t launch_jacobi_f64(const Op& op, const double* g_in, const double* u,
                               int L, cudaStream_t st);
 cudaError_t launch_site_inverse_f64(const Op& op, const double* u, double* g_out, int L,
                                     cudaStream_t st);
+
+// ---- dslash_x3.cu (the same FP64 operations with the hopping sums on the FP32 lanes)
+cudaError_t launch_link_split(const Op& op, cudaStream_t st);
+cudaError_t launch_apply_x3(const Op& op, const double* x, double* y, int L, cudaStream_t st);
+cudaError_t launch_resid_x3(const Op& op, const double* x, const double* b, double* y, int L,
+                            cudaStream_t st);
+cudaError_t launch_jacobi_x3(const Op& op, const double* g_in, const double* u, double* g_out,
+                             int L, cudaStream_t st);
+// Kernels one FP64 stencil launch takes (the x3 form adds its exponent pre-pass).
+inline int stencil_kernels(const Op& op) { return op.apply_form == 1 ? 2 : 1; }
 
 // ---- sweep_lp.cu, sweep_f32.cu, sweep_bf16.cu: the low-precision preconditioner.  Its private
 // blocks (u_lp, g_lp) are component-major, [spin*3+colour][site][rhs], one complex number per

@@ -103,7 +103,7 @@ extern "C" int jacobi_precond_noalloc(wd_ctx* ctx, const void* R, void* G, int L
     wd_ctx_count_launches(ctx, WD_K_SITE_INV, 1);
     for (int i = 1; i < j && e == cudaSuccess; ++i) {
       e = launch_jacobi_f64(op, cur, r, nxt, L, s);
-      wd_ctx_count_launches(ctx, WD_K_JACOBI, 1);
+      wd_ctx_count_launches(ctx, WD_K_JACOBI, stencil_kernels(op));
       double* t = cur;
       cur = nxt;
       nxt = t;
