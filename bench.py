@@ -69,6 +69,15 @@ DF_OPS = 8 * (12 * 8 + 6 * (2 * 3 + 2 * 11) + 12 * 4 * 11 + 24 * 8) + 8 * 30 + 1
 # lane-pair sums (12 x (2 x 2 x 29 + 8)) and 30 for their bounds; U + kappa H and the stores.
 DF_OPS_GRID = 8 * (12 * 8 + 6 * (2 * 2 * 14 + 8) + 16 + 24 * 8) + 8 * 30 \
     + 12 * (2 * 2 * 29 + 8) + 30 + 24 * 11 + 24 * 3
+# FP64-pipe operations per site and RHS of the FP32-lane form of the FP64 stencils
+# (csrc/dslash_x3.cu, wd_set_apply_form 1): the spin projections (8 hops x 12 real FMAs), joining
+# the three levels of the 24 hopping sums (2 adds each), the 24 final FMAs with kappa, and the two
+# Hermitian 6x6 site blocks (6 real x complex products and 15 complex entries used twice, 4 FMAs per
+# complex product: 2 x (12 + 120)).  The hopping products themselves run on the FP32 lanes: 288
+# packed lane-pair products of 24 operations (48 lane operations), 48 row combinations of ~38 lane
+# operations, 96 exact three-way splits of ~15 and the joins' 360 bit-field operations.
+X3_FP64_OPS = 8 * 12 + 24 * 2 + 24 + 2 * (12 + 120)
+X3_FP32_OPS = 288 * 48 + 48 * 38 + 96 * 15 + 360
 METRIC = "time-to-solution at true resid 1e-12 for L RHS; Dslash HBM GB/s vs peak"
 FLOP_APPLY = 1824          # flop per site per RHS of A (1320 hopping + 504 clover)
 FLOP_JACOBI = 1872         # flop per site per RHS of one Jacobi sweep A_D^{-1}(U + kappa H G)
@@ -756,10 +765,14 @@ def main():
                   "df_dirs": "df"}[args.precision]
     df_tile = wd.wd_tuned_tile(ctx, L_RHS, precision=4) if sweep_prec == "df" else None
     per_kernel = {}
+    stencil_form = wd.wd_get_apply_form(ctx)
     for cls in ("dslash_jacobi_lp", "dslash_jacobi", "dslash_apply"):
         n, ms = prof.get(cls, (0, 0.0))
         if not n:
             continue
+        # the FP32-lane form launches an exponent pre-pass with each FP64 stencil
+        per_launch = 2 if stencil_form == 1 and cls in ("dslash_apply", "dslash_jacobi") else 1
+        n //= per_launch
         avg_s = ms / n / 1e3
         kprec = sweep_prec if cls == "dslash_jacobi_lp" else "fp64"
         f32 = kprec in ("fp32", "bf16")
@@ -785,6 +798,18 @@ def main():
                 "bound": "alu", "achieved": round(tops, 3), "peak": round(alu["fp32_lane_tops"], 2),
                 "unit": "T FP32 lane ops/s", "frac": round(tops / alu["fp32_lane_tops"], 4),
                 "peak_source": alu_source + " x 128 FP32 lanes", "fp32_ops_per_site_rhs": ops}
+        elif not f32 and stencil_form == 1:
+            # the FP32-lane form: FP64 pipe and FP32 lanes both carry work; the FP64 pipe is the
+            # busier one (ncu)
+            ops64 = X3_FP64_OPS * V * L_RHS / avg_s / 1e12
+            ops32 = X3_FP32_OPS * V * L_RHS / avg_s / 1e12
+            fig["binding_roofline"] = {
+                "bound": "alu", "achieved": round(ops64, 4), "peak": round(alu["fp64_tflops"] / 2, 4),
+                "unit": "T FP64-pipe ops/s", "frac": round(ops64 / (alu["fp64_tflops"] / 2), 4),
+                "peak_source": alu_source + " x 2 FP64 lanes/clk", "fp64_ops_per_site_rhs": X3_FP64_OPS,
+                "fp32_lane_ops_per_site_rhs": X3_FP32_OPS,
+                "fp32_lane_frac": round(ops32 / alu["fp32_lane_tops"], 4),
+                "form": "hopping sums on the FP32 lanes (wd_set_apply_form 1)"}
         elif not f32:
             fig["binding_roofline"] = {
                 "bound": "alu", "achieved": round(tflops, 4), "peak": round(alu["fp64_tflops"], 4),
@@ -794,7 +819,7 @@ def main():
                     "traffic": ncu_traffic(cls, kprec),
                     "algorithmic_bytes_per_launch": nbytes, "flop_per_site_rhs": flop_unit,
                     "avg_launch_ms": round(avg_s * 1e3, 4), "launches": n,
-                    "total_ms": round(ms, 2)})
+                    "kernels_per_launch": per_launch, "total_ms": round(ms, 2)})
         per_kernel[cls] = fig
     dom = max(per_kernel, key=lambda k: per_kernel[k]["total_ms"])
     roofline = dict(per_kernel[dom])

@@ -149,8 +149,8 @@ WD_DEV void hop_x3_spin(const double* __restrict__ xp, const float4* __restrict_
   const int phu = ((((SP == 0 ? 0x19 : 0x31) >> (2 * mu)) & 3) + (dir > 0 ? 2 : 0)) & 3;
   // (G_mu d)_SP: (a, b) = the lanes of d after the phase's swap, with signs sa, sb; h = up -dir G d
   const bool swd = phd & 1;
-  const double sa = ((phd == 1 || phd == 2) ? -1.0 : 1.0) * (dir > 0 ? -1.0 : 1.0);
-  const double sb = (phd >= 2 ? -1.0 : 1.0) * (dir > 0 ? -1.0 : 1.0);
+  const bool na = (phd == 1 || phd == 2) != (dir > 0), nb = (phd >= 2) != (dir > 0);
+  const double sa = na ? -1.0 : 1.0, sb = nb ? -1.0 : 1.0;
   float2 b1[3], nb1[3], b2[3], b3[3];
 #pragma unroll
   for (int col = 0; col < 3; ++col) {
