@@ -672,6 +672,13 @@ def main():
     ms_step = ms_total / args.steps
     ok = all(i["status"] == wd.WD_OK and i["max_true_resid"] <= TOL for i in infos)
     X_main = X.clone()   # this form's solution, compared per column with the FP64 form's below
+    # how far the recursive residual R (R -= zeta W + Y) drifted from B - A X over the solve, per
+    # column relative to ||b||, with B - A X from the library's FP64 stencil (outside the timing)
+    R_rec = wd.wd_copy_residual(ctx, torch.empty_like(B))
+    R_true = B - wd.wd_apply(ctx, X_main)
+    gap = ((R_rec - R_true).reshape(-1, L_RHS).norm(dim=0) / B.reshape(-1, L_RHS).norm(dim=0))
+    residual_gap = float(gap.max().item())
+    del R_rec, R_true
 
     # ---- end to end through the C-ABI with pinned host buffers.  Every step gets its own X0 = 0
     # host buffer, prepared before the timed region like B; inside it are the copies of B and X0
@@ -845,6 +852,7 @@ def main():
                      "restarts": infos[-1]["restarts"],
                      "fallbacks": infos[-1]["fallbacks"],
                      "true_resid_per_column": [float(f"{v:.3e}") for v in infos[-1]["true_resid"]],
+                     "recursive_vs_true_residual_gap": float(f"{residual_gap:.3e}"),
                      "rel_diff_vs_fp64_per_column": (None if col_diff is None else
                                                      [float(f"{v:.3e}") for v in col_diff])},
            "kernels": {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in prof.items() if n or ms}}

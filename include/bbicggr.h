@@ -206,6 +206,13 @@ typedef struct {
  * job's non-OK status; argument and CUDA errors return before any work. */
 int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream);
 
+/* Copies the recursive residual R of the algorithm box (Sec. 2) as the last solve on ctx left it --
+ * updated by R -= zeta W + Y every iteration, never recomputed from X -- to R (N x L, host or
+ * device), so that a caller can measure how far it drifted from B - A X (the true residual,
+ * Sec. 1).  L must be the last solve's; WD_EINVAL otherwise or before any solve.  Synchronises
+ * the stream. */
+int wd_copy_residual(wd_ctx* ctx, void* R, int L, void* stream);
+
 void bbicggr_default_opts(bbicggr_opts* opts);
 const char* wd_strerror(int code);
 const char* wd_last_error(void);

@@ -120,6 +120,8 @@ def lib():
     L.wd_link_reals.restype = C.c_int
     L.wd_set_link_reals.argtypes = [vp, i]
     L.wd_set_link_reals.restype = C.c_int
+    L.wd_copy_residual.argtypes = [vp, vp, i, vp]
+    L.wd_copy_residual.restype = C.c_int
     L.wd_set_apply_form.argtypes = [vp, i]
     L.wd_set_apply_form.restype = C.c_int
     L.wd_get_apply_form.argtypes = [vp]
@@ -437,6 +439,13 @@ def wd_link_reals(ctx: Context) -> int:
 def wd_set_link_reals(ctx: Context, reals: int) -> None:
     """Choose the link format of the low-precision sweeps (12 needs special unitary links)."""
     _check(lib().wd_set_link_reals(ctx.handle, int(reals)))
+
+
+def wd_copy_residual(ctx: Context, R):
+    """Copy the last solve's recursive residual block into R (a tensor shaped like B)."""
+    pr, L, k = _ptr_and_L(R, "R")
+    _check(lib().wd_copy_residual(ctx.handle, pr, L, _stream(None)))
+    return R
 
 
 def wd_set_apply_form(ctx: Context, form: int) -> None:

@@ -109,6 +109,7 @@ struct wd_ctx {
   int device = 0;
   // solver workspace for the current L
   int L = 0;
+  int solved_L = 0;        // L of the last solve, whose recursive residual is in blk[B_R]
   DevBuf blk[13];          // R P V W F U G Y Rt T (always); B Xs X0 (on demand)
   DevBuf part;             // reduction partials
   SolverState* st = nullptr;
@@ -1185,6 +1186,7 @@ int bbicggr_solve(wd_ctx* c, const void* B, void* X, int L, int j, double tol,
     CU(cudaMemcpyAsync(X, Xd, bytes, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
   }
+  c->solved_L = L;
   if (info) {
     info->status = status;
     info->iters = iters;
@@ -1657,7 +1659,20 @@ extern "C" int bbicggr_solve_batch(bbicggr_job* jobs, int njobs, void* stream) {
       in.history_count = n;
     }
     in.seconds = secs;
+    c->solved_L = jb.L;
     if (status != WD_OK && worst == WD_OK) worst = status;
   }
   return worst;
+}
+
+extern "C" int wd_copy_residual(wd_ctx* c, void* R, int L, void* stream) {
+  if (!c || !R) { set_err("ctx or R is NULL"); return WD_EINVAL; }
+  if (c->solved_L == 0 || L != c->solved_L) {
+    set_err("no solve with L = %d on this context (last: %d)", L, c->solved_L);
+    return WD_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CU(cudaMemcpyAsync(R, c->blk[B_R].d(), block_bytes(c, L), cudaMemcpyDefault, s));
+  CU(cudaStreamSynchronize(s));
+  return WD_OK;
 }

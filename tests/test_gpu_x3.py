@@ -177,3 +177,27 @@ def test_x3_needs_unitary_links(wd):
     X = I.gaussian_block(dims, 2, seed=2)
     Yo = O.WilsonClover(links, dims, 0.12, 1.0).apply(X)
     assert max_elem_rel(host(wd.wd_apply(ctx, dev(X))), Yo) < X3_TOL
+
+
+@pytest.mark.parametrize("kappa,precision", [(0.13, 0), (0.13, 5), (0.134, 5)])
+def test_recursive_residual_stays_on_the_true_residual(wd, kappa, precision):
+    """The recursive residual R (R -= zeta W + Y each iteration, never recomputed from X) stays
+    on B - A X to FP64 accuracy through a whole solve: the products W = A F and Y = A G carry no
+    error the recursion could accumulate beyond ~1e-15 of ||B||."""
+    dims = (8, 8, 8, 16)
+    links = I.random_links(dims, 0.2, seed=0)
+    B = I.z4_noise(dims, 12, seed=1)
+    ctx = wd.wd_create(dev(links), dims, kappa, 1.0)
+    with pytest.raises(wd.WDError):
+        wd.wd_copy_residual(ctx, torch.empty_like(dev(B)))      # no solve yet
+    X, info = wd.bbicggr_solve(ctx, dev(B), j=12, tol=1e-12, precision=precision, maxit=2000)
+    assert info["status"] == wd.WD_OK
+    R = host(wd.wd_copy_residual(ctx, torch.empty_like(dev(B))))
+    op = O.WilsonClover(links, dims, kappa, 1.0)
+    T = B - op.apply(host(X))
+    V = int(np.prod(dims))
+    gap = (np.linalg.norm((R - T).reshape(V * 12, -1), axis=0)
+           / np.linalg.norm(B.reshape(V * 12, -1), axis=0))
+    assert gap.max() <= 1e-13
+    with pytest.raises(wd.WDError):
+        wd.wd_copy_residual(ctx, torch.empty_like(dev(B[..., :4])))   # another L
