@@ -241,8 +241,17 @@ def oracle_full_solve(cfg, threads):
     t0 = time.perf_counter()
     X, st, k, restarts, mvm, tr = cpp.CppOracle(links, cfg["dims"], cfg["kappa"], CSW).solve(
         B, cfg["j"])
-    return {"seconds": round(time.perf_counter() - t0, 4), "threads": used, "status": st,
-            "iters": k, "mvm_per_column": mvm, "max_true_resid": float(tr.max())}
+    sec = time.perf_counter() - t0
+    return {"seconds": round(sec, 4), "threads": used, "status": st,
+            "iters": k, "mvm_per_column": mvm, "max_true_resid": float(tr.max()),
+            "gflops": round(solve_flop(cfg, mvm) / sec / 1e9, 2)}
+
+
+def solve_flop(cfg, mvm_per_column):
+    """Stencil flop of a solve: the paper's #MVM count per column times L RHS times 1824 flop per
+    site and RHS (each Jacobi step counted as one MVM, as Table 1 counts them)."""
+    import numpy as np
+    return mvm_per_column * cfg["L"] * int(np.prod(cfg["dims"])) * FLOP_APPLY
 
 
 class OracleSample:
@@ -558,8 +567,10 @@ def gpu_small_solves(wd, I, dev, prec):
         t0 = time.perf_counter()
         _, info = wd.bbicggr_solve(ctx, B, j=cfg["j"], tol=TOL, precision=prec)
         torch.cuda.synchronize(dev)
-        out[name] = {"seconds": round(time.perf_counter() - t0, 5), "iters": info["iters"],
-                     "max_true_resid": info["max_true_resid"]}
+        sec = time.perf_counter() - t0
+        out[name] = {"seconds": round(sec, 5), "iters": info["iters"],
+                     "max_true_resid": info["max_true_resid"],
+                     "gflops": round(solve_flop(cfg, info["mvm_paper"] // cfg["L"]) / sec / 1e9, 2)}
         wd.wd_destroy(ctx)
     return out
 

@@ -688,6 +688,8 @@ void wd_destroy(wd_ctx* c) {
   cudaFree(c->op.links32);
   cudaFree(c->op.clov_inv32);
   cudaFree(c->op.clov_bound32);
+  cudaFree(c->op.links32s);
+  cudaFree(c->op.clov_inv32s);
   cudaFree(c->op.links_x3);
   cudaFree(c->op.xexp);
   for (auto& b : c->blk) b.release();
@@ -715,6 +717,8 @@ static int create_impl(wd_ctx* c, const void* links, const int dims[4], cudaStre
   CU(cudaMalloc(&op.links32, V * 4 * 18 * sizeof(float)));
   CU(cudaMalloc(&op.clov_inv32, V * 2 * CLOV_REALS * sizeof(float)));
   CU(cudaMalloc(&op.clov_bound32, V * 2 * sizeof(float)));
+  CU(cudaMalloc(&op.links32s, V * 4 * 5 * sizeof(float4)));
+  CU(cudaMalloc(&op.clov_inv32s, V * 2 * (CLOV_REALS / 4) * sizeof(float4)));
   CU(cudaMemcpyAsync(op.links, links, lbytes, cudaMemcpyDefault, s));
   // [0]: a singular A_D block; [1]: a link that is not special unitary; [2]: a link with a row or
   // column of norm above 1

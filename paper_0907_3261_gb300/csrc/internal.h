@@ -29,6 +29,11 @@ struct Op {
   // max(sum_j |Re D_ij|, sum_j |Im D_ij|), rounded up -- a bound on the partial sums of a row
   // times a vector in units of the vector's largest real part.
   float* clov_bound32;
+  // Site-major FP32 copies for the grid-sum double-float sweep, read in 16-byte loads: the links
+  // [site][mu][20 floats] (9 entries (re, im) row by row, two zeros) and A_D^{-1}
+  // [site][chirality][36 floats] (the packed blocks of clov_inv32).
+  float4* links32s;
+  float4* clov_inv32s;
   // The FP32-lane form of the FP64 stencil (dslash_x3.cu): the links cut into three FP32 levels,
   // [site][mu][level][entry] as (re, re, im, im) (null when the links are not unitary), a scratch
   // of V * WD_LMAX exponents, and the form in use (1: this one, 0: the FP64-pipe kernel).

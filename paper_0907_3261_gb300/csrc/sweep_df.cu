@@ -473,8 +473,30 @@ sweep_df2_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4*
 
 WD_DEV float habs_max(const P2& z, float m) { return fmaxf(m, fmaxf(fabsf(z.hi.x), fabsf(z.hi.y))); }
 
+// A link from the site-major copy ([site][mu][20 floats]: the 9 entries (re, im) row by row, then
+// two zeros), rows 0 and 1 in three 16-byte loads and row 2 rebuilt (link12) or loaded.
+WD_DEV void link_sm(const float4* __restrict__ U, bool link12, Cx<float> m[3][3]) {
+  const float4 a = __ldg(U), b = __ldg(U + 1), c = __ldg(U + 2);
+  m[0][0] = cmake<float>(a.x, a.y);
+  m[0][1] = cmake<float>(a.z, a.w);
+  m[0][2] = cmake<float>(b.x, b.y);
+  m[1][0] = cmake<float>(b.z, b.w);
+  m[1][1] = cmake<float>(c.x, c.y);
+  m[1][2] = cmake<float>(c.z, c.w);
+  if (link12) {
+    m[2][0] = conj(cmul(m[0][1], m[1][2]) - cmul(m[0][2], m[1][1]));
+    m[2][1] = conj(cmul(m[0][2], m[1][0]) - cmul(m[0][0], m[1][2]));
+    m[2][2] = conj(cmul(m[0][0], m[1][1]) - cmul(m[0][1], m[1][0]));
+  } else {
+    const float4 d = __ldg(U + 3), e = __ldg(U + 4);
+    m[2][0] = cmake<float>(d.x, d.y);
+    m[2][1] = cmake<float>(d.z, d.w);
+    m[2][2] = cmake<float>(e.x, e.y);
+  }
+}
+
 // The hopping term H x at (s, r) as hopping2, the link products summed on the hop's grid.
-WD_DEV void hopping3(const float4* __restrict__ x, const float2* __restrict__ links, const Geom& g,
+WD_DEV void hopping3(const float4* __restrict__ x, const float4* __restrict__ links, const Geom& g,
                      int s, const int c[4], int r, int L, bool link12, P2 au[2][3], P2 ad[2][3],
                      float2 m1) {
   const size_t V = (size_t)g.V;
@@ -506,7 +528,7 @@ WD_DEV void hopping3(const float4* __restrict__ x, const float2* __restrict__ li
     const float2 sigma = grid_bias(hm, 3);
     const float2 nsigma = make_float2(-sigma.x, -sigma.y);
     Cx<float> m[3][3];
-    link(links + (size_t)mu * 9 * V + (fwd ? s : sn), V, link12, m);
+    link_sm(links + (size_t)((fwd ? s : sn) * 4 + mu) * 5, link12, m);
     if (!fwd) {   // W = m^H
 #pragma unroll
       for (int a = 0; a < 3; ++a)
@@ -545,16 +567,27 @@ WD_DEV void hopping3(const float4* __restrict__ x, const float2* __restrict__ li
   }
 }
 
-// Row i of a packed Hermitian 6x6 FP32 block times v (as herm6_row2), summed on the grid sigma.
-WD_DEV P2 herm6_row3(const float* __restrict__ mat, size_t stride, int i, const P2 v[6],
-                     float2 sigma, float2 nsigma, float2 m1) {
+
+// Row i of a packed Hermitian 6x6 block held in registers (cl: the 36 reals of the packed block,
+// the diagonal first, then the strictly-lower pairs) times v, summed on the grid sigma; the same
+// products in the same order as herm6_row3, the entries indexed at compile time.
+template <int I>
+WD_DEV P2 herm6_row3r(const float cl[CLOV_REALS], const P2 v[6], float2 sigma, float2 nsigma,
+                      float2 m1) {
   float2 SX, LX, SY, LY;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
-    const int t = c_h6_off[i][j];
-    const float sg = c_h6_sgn[i][j];
-    const float re = __ldg(mat + t * stride);
-    const float im = sg * __ldg(mat + (t + (sg != 0.f)) * stride);
+    float re, im;
+    if (j == I) {
+      re = cl[I];
+      im = 0.f * cl[I];
+    } else if (j < I) {
+      re = cl[tri_index(I, j)];
+      im = cl[tri_index(I, j) + 1];
+    } else {
+      re = cl[tri_index(j, I)];
+      im = -cl[tri_index(j, I) + 1];
+    }
     if (j == 0) {
       gmul(SX, LX, dup(re), v[0], sigma, m1);
       gmul(SY, LY, dup(im), v[0], sigma, m1);
@@ -566,10 +599,34 @@ WD_DEV P2 herm6_row3(const float* __restrict__ mat, size_t stride, int i, const 
   return gcombine(SX, LX, SY, LY, nsigma);
 }
 
+// One chirality block of the site-major inverse copy ([site][chirality][36 floats]) into registers.
+WD_DEV void clover_block(const float4* __restrict__ p, float cl[CLOV_REALS]) {
+#pragma unroll
+  for (int q = 0; q < CLOV_REALS / 4; ++q) {
+    const float4 t = __ldg(p + q);
+    cl[4 * q] = t.x;
+    cl[4 * q + 1] = t.y;
+    cl[4 * q + 2] = t.z;
+    cl[4 * q + 3] = t.w;
+  }
+}
+
+// The six rows of one chirality block, stored as they are formed.
+template <typename TY>
+WD_DEV void herm6_rows3r(const float cl[CLOV_REALS], const P2 vin[6], float2 sigma, float2 nsigma,
+                         float2 m1, TY* y, size_t V, int L, int s, int ch, int r) {
+  stq2(at(y, V, L, s, ch * 6 + 0, r), herm6_row3r<0>(cl, vin, sigma, nsigma, m1), m1);
+  stq2(at(y, V, L, s, ch * 6 + 1, r), herm6_row3r<1>(cl, vin, sigma, nsigma, m1), m1);
+  stq2(at(y, V, L, s, ch * 6 + 2, r), herm6_row3r<2>(cl, vin, sigma, nsigma, m1), m1);
+  stq2(at(y, V, L, s, ch * 6 + 3, r), herm6_row3r<3>(cl, vin, sigma, nsigma, m1), m1);
+  stq2(at(y, V, L, s, ch * 6 + 4, r), herm6_row3r<4>(cl, vin, sigma, nsigma, m1), m1);
+  stq2(at(y, V, L, s, ch * 6 + 5, r), herm6_row3r<5>(cl, vin, sigma, nsigma, m1), m1);
+}
+
 template <typename TY>
 __global__ void __launch_bounds__(128, 4)
 sweep_df3_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4* __restrict__ u,
-                 const float2* __restrict__ links, const float* __restrict__ clov_inv,
+                 const float4* __restrict__ links, const float4* __restrict__ clov_inv,
                  const float* __restrict__ clov_bound, Geom g, int L, float kappa, int link12) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= g.V * L) return;
@@ -600,10 +657,9 @@ sweep_df3_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4*
     const float bnd = __ldg(clov_bound + (size_t)ch * V + s) * vm * (1.f + 0x1p-16f);
     const float2 sigma = grid_bias(bnd, 2);
     const float2 nsigma = make_float2(-sigma.x, -sigma.y);
-    const float* mm = clov_inv + (size_t)ch * CLOV_REALS * V + s;
-#pragma unroll 1
-    for (int i = 0; i < 6; ++i)
-      stq2(at(y, V, L, s, ch * 6 + i, r), herm6_row3(mm, V, i, vin, sigma, nsigma, m1), m1);
+    float cl[CLOV_REALS];
+    clover_block(clov_inv + ((size_t)s * 2 + ch) * (CLOV_REALS / 4), cl);
+    herm6_rows3r(cl, vin, sigma, nsigma, m1, y, V, L, s, ch, r);
   }
 }
 
@@ -613,7 +669,7 @@ sweep_df3_kernel(const float4* __restrict__ x, TY* __restrict__ y, const float4*
 template <typename TY>
 __global__ void __launch_bounds__(128)
 site_inverse_df_kernel(const double* __restrict__ u, float4* __restrict__ u_df, TY* __restrict__ y,
-                       const float* __restrict__ clov_inv, const float* __restrict__ clov_bound,
+                       const float4* __restrict__ clov_inv, const float* __restrict__ clov_bound,
                        int V, int L) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= V * L) return;
@@ -638,10 +694,9 @@ site_inverse_df_kernel(const double* __restrict__ u, float4* __restrict__ u_df, 
     const float bnd = __ldg(clov_bound + (size_t)ch * V + s) * vm * (1.f + 0x1p-16f);
     const float2 sigma = grid_bias(bnd, 2);
     const float2 nsigma = make_float2(-sigma.x, -sigma.y);
-    const float* mm = clov_inv + (size_t)ch * CLOV_REALS * V + s;
-#pragma unroll 1
-    for (int i = 0; i < 6; ++i)
-      stq2(at(y, (size_t)V, L, s, ch * 6 + i, r), herm6_row3(mm, V, i, vin, sigma, nsigma, m1), m1);
+    float cl[CLOV_REALS];
+    clover_block(clov_inv + ((size_t)s * 2 + ch) * (CLOV_REALS / 4), cl);
+    herm6_rows3r(cl, vin, sigma, nsigma, m1, y, (size_t)V, L, s, ch, r);
   }
 }
 
@@ -653,9 +708,9 @@ cudaError_t launch_site_inverse_df(const Op& op, const double* u, void* u_df, vo
   float4* ud = static_cast<float4*>(u_df);
   if (g_df)
     site_inverse_df_kernel<float4><<<grid, 128, 0, st>>>(u, ud, static_cast<float4*>(g_df),
-                                                         op.clov_inv32, op.clov_bound32, op.g.V, L);
+                                                         op.clov_inv32s, op.clov_bound32, op.g.V, L);
   else
-    site_inverse_df_kernel<double><<<grid, 128, 0, st>>>(u, ud, g64, op.clov_inv32,
+    site_inverse_df_kernel<double><<<grid, 128, 0, st>>>(u, ud, g64, op.clov_inv32s,
                                                          op.clov_bound32, op.g.V, L);
   return cudaGetLastError();
 }
@@ -688,13 +743,12 @@ cudaError_t launch_jacobi_df(const Op& op, const void* g_in, const void* u_df, v
   float4* gd = static_cast<float4*>(g_df);
   if (packed == 2) {
     const unsigned grid = (unsigned)(((long long)op.g.V * L + block - 1) / block);
-    const float2* links = reinterpret_cast<const float2*>(op.links32);
     if (gd)
-      sweep_df3_kernel<float4><<<grid, block, 0, st>>>(x, gd, u, links, op.clov_inv32,
+      sweep_df3_kernel<float4><<<grid, block, 0, st>>>(x, gd, u, op.links32s, op.clov_inv32s,
                                                        op.clov_bound32, op.g, L, (float)op.kappa,
                                                        op.link12);
     else
-      sweep_df3_kernel<double><<<grid, block, 0, st>>>(x, g64, u, links, op.clov_inv32,
+      sweep_df3_kernel<double><<<grid, block, 0, st>>>(x, g64, u, op.links32s, op.clov_inv32s,
                                                        op.clov_bound32, op.g, L, (float)op.kappa,
                                                        op.link12);
     return cudaGetLastError();

@@ -25,6 +25,21 @@ __global__ void clover_to_cm_kernel(const double* __restrict__ cl, float* __rest
       out[(size_t)(ch * CLOV_REALS + t) * V + s] = (float)cl[((size_t)s * 2 + ch) * CLOV_REALS + t];
 }
 
+// The site-major copies of the double-float sweep (same FP32 values as links32 and clov_inv32).
+__global__ void operator_to_sm_kernel(const double* __restrict__ links, const double* __restrict__ cl,
+                                      float* __restrict__ lsm, float* __restrict__ csm, int V) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  for (int mu = 0; mu < 4; ++mu) {
+    const double* p = links + 18 * ((size_t)s * 4 + mu);
+    float* q = lsm + 20 * ((size_t)s * 4 + mu);
+    for (int k = 0; k < 18; ++k) q[k] = (float)p[k];
+    q[18] = 0.f;
+    q[19] = 0.f;
+  }
+  for (int k = 0; k < 2 * CLOV_REALS; ++k) csm[(size_t)s * 2 * CLOV_REALS + k] = (float)cl[(size_t)s * 2 * CLOV_REALS + k];
+}
+
 // Sets flags[0] when some link's third row differs from conj(row0 x row1) by more than tol in
 // some entry, and flags[1] when some row or column has norm above 1 + tol (checked in FP64 on the
 // caller's links).
@@ -80,6 +95,9 @@ cudaError_t launch_lp_operator_copies(const Op& op, int* flags, cudaStream_t st)
   const unsigned grid = (unsigned)((op.g.V + threads - 1) / threads);
   links_to_cm_kernel<<<grid, threads, 0, st>>>(op.links, op.links32, op.g.V);
   clover_to_cm_kernel<<<grid, threads, 0, st>>>(op.clov_inv, op.clov_inv32, op.g.V);
+  operator_to_sm_kernel<<<grid, threads, 0, st>>>(op.links, op.clov_inv,
+                                                  reinterpret_cast<float*>(op.links32s),
+                                                  reinterpret_cast<float*>(op.clov_inv32s), op.g.V);
   clover_bound_kernel<<<grid, threads, 0, st>>>(op.clov_inv, op.clov_bound32, op.g.V);
   const unsigned grid4 = (unsigned)((4LL * op.g.V + threads - 1) / threads);
   su3_check_kernel<<<grid4, threads, 0, st>>>(op.links, op.g.V, LINK12_TOL, flags);
