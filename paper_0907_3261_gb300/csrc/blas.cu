@@ -17,6 +17,7 @@ namespace {
 constexpr int TS_THREADS = 256;
 constexpr int CH = 32;                     // rows per chunk
 constexpr int CHE = CH * WD_LMAX;          // complex entries per chunk at most
+constexpr int CHU = 64;                    // rows per chunk of update_u (L = 12: 768 entries, 3 per thread)
 
 WD_DEV Cx<double> ld2(const double* p, size_t e) {
   double2 v = *reinterpret_cast<const double2*>(p + 2 * e);
@@ -396,7 +397,7 @@ WD_DEV void pmac_coef(P2& X, P2& Y, const CDF& g, P2 b, float2 m1) {
 __global__ void __launch_bounds__(TS_THREADS)
 update_u_df_kernel(const double* __restrict__ P, const double* __restrict__ V, double* __restrict__ U,
                    int L, long long rows, const SolverState* __restrict__ st) {
-  __shared__ P2 Ss[CHE];
+  __shared__ P2 Ss[CHU * WD_LMAX];
   __shared__ CDF al[WD_LMAX * WD_LMAX];
   if (st->status != ST_OK) return;
   const float2 m1 = make_float2(-1.f, -1.f);
@@ -406,20 +407,43 @@ update_u_df_kernel(const double* __restrict__ P, const double* __restrict__ V, d
   const float2 a2 = make_float2(z.im.hi, -z.im.hi), na2 = make_float2(-z.im.hi, z.im.hi);
   const float2 a2lo = make_float2(z.im.lo, -z.im.lo);
   for (int e = threadIdx.x; e < L * L; e += blockDim.x) al[e] = cdf_of(st->alpha[e]);
-  const long long nchunks = (rows + CH - 1) / CH;
+  const long long nchunks = (rows + CHU - 1) / CHU;
+  // The next chunk's P and V are loaded into registers while the current one is computed (a
+  // thread holds at most CHU * WD_LMAX / TS_THREADS = 4 elements of a chunk).
+  double2 pn[CHU * WD_LMAX / TS_THREADS], vn[CHU * WD_LMAX / TS_THREADS];
+  auto fetch = [&](long long ck) {
+    if (ck >= nchunks) return;
+    const long long r0 = ck * CHU;
+    const int cnt = (int)min((long long)CHU, rows - r0) * L;
+    const size_t e0 = (size_t)r0 * L;
+#pragma unroll
+    for (int q = 0; q < CHU * WD_LMAX / TS_THREADS; ++q) {
+      const int e = threadIdx.x + q * TS_THREADS;
+      if (e < cnt) {
+        pn[q] = reinterpret_cast<const double2*>(P)[e0 + e];
+        vn[q] = reinterpret_cast<const double2*>(V)[e0 + e];
+      }
+    }
+  };
+  fetch(blockIdx.x);
   for (long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
-    const long long r0 = ck * CH;
-    const int nr = (int)min((long long)CH, rows - r0);
+    const long long r0 = ck * CHU;
+    const int nr = (int)min((long long)CHU, rows - r0);
     const int cnt = nr * L;
     const size_t e0 = (size_t)r0 * L;
     __syncthreads();
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      P2 sv = ldp2(P, e0 + e);
-      const P2 v = ldp2(V, e0 + e);
-      pmac_dd(sv, a1, na1, a1lo, v, m1);          // P - zeta V
-      pmac_dd(sv, a2, na2, a2lo, pswap(v), m1);
-      Ss[e] = sv;
+#pragma unroll
+    for (int q = 0; q < CHU * WD_LMAX / TS_THREADS; ++q) {
+      const int e = threadIdx.x + q * TS_THREADS;
+      if (e < cnt) {
+        P2 sv = p2_split(pn[q]);
+        const P2 v = p2_split(vn[q]);
+        pmac_dd(sv, a1, na1, a1lo, v, m1);          // P - zeta V
+        pmac_dd(sv, a2, na2, a2lo, pswap(v), m1);
+        Ss[e] = sv;
+      }
     }
+    fetch(ck + gridDim.x);
     __syncthreads();
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
       const int n = e / L, b = e - (e / L) * L;
@@ -609,7 +633,7 @@ cudaError_t launch_solve_gamma(SolverState* st, int L, cudaStream_t s) {
 cudaError_t launch_update_u(const double* P, const double* V, double* U, int L, long long rows,
                             const SolverState* st, cudaStream_t s, bool df) {
   if (df)
-    update_u_df_kernel<<<blocks_for(rows), TS_THREADS, 0, s>>>(P, V, U, L, rows, st);
+    update_u_df_kernel<<<blocks_for((rows + 1) / 2), TS_THREADS, 0, s>>>(P, V, U, L, rows, st);
   else
     update_u_kernel<<<blocks_for(rows), TS_THREADS, 0, s>>>(P, V, U, L, rows, st);
   return cudaGetLastError();

@@ -201,3 +201,15 @@ def test_recursive_residual_stays_on_the_true_residual(wd, kappa, precision):
     assert gap.max() <= 1e-13
     with pytest.raises(wd.WDError):
         wd.wd_copy_residual(ctx, torch.empty_like(dev(B[..., :4])))   # another L
+
+
+def test_x3_full_size_element_wise(wd):
+    """The bench lattice (16^3 x 32, L = 12, near-critical kappa): every entry of the FP32-lane
+    form's A X against the oracle and against the FP64-pipe form."""
+    dims = (16, 16, 16, 32)
+    links = I.random_links(dims, 0.2, seed=0)
+    X = I.z4_noise(dims, 12, seed=7)
+    Y1, Y0 = both_forms(wd, links, dims, 0.134, 1.0, X)
+    Yo = O.WilsonClover(links, dims, 0.134, 1.0).apply(X)
+    assert max_elem_rel(Y1, Yo) < X3_TOL
+    assert max_elem_rel(Y1, Y0) < X3_TOL
