@@ -186,10 +186,22 @@ def gpu_id_for_smi(torch, dev) -> str:
 
 
 # ---------------------------------------------------------------- traffic from committed ncu summaries
-def csrc_sha() -> str:
+# The source files each profiled kernel class is compiled from (with the shared headers): its
+# recorded DRAM traffic stays valid while these are unchanged.
+KERNEL_SOURCES = {
+    ("dslash_jacobi_lp", "df"): ["sweep_df.cu", "common.cuh", "elem.cuh", "internal.h"],
+    ("dslash_jacobi_lp", "fp32"): ["sweep_lp.cuh", "sweep_f32.cu", "sweep_lp.cu", "common.cuh",
+                                   "elem.cuh", "internal.h"],
+    ("dslash_apply", "fp64"): ["dslash_x3.cu", "dslash.cu", "common.cuh", "spin.cuh", "internal.h"],
+}
+
+
+def csrc_sha(files=None) -> str:
+    """Hash of the library sources (all of csrc/, or the given file names in it)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_0907_3261_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    names = sorted(files) if files else sorted(os.listdir(d))
+    for name in names:
         if name.endswith((".cu", ".cuh", ".h")):
             h.update(open(os.path.join(d, name), "rb").read())
     return h.hexdigest()[:16]
@@ -197,11 +209,12 @@ def csrc_sha() -> str:
 
 def ncu_traffic(kernel_class: str, precision: str):
     """DRAM bytes per launch recorded in profiles/*.md as
-    ``bench-traffic: <class> <precision> <bytes> <csrc sha>``; None if absent or stale."""
+    ``bench-traffic: <class> <precision> <bytes> <sources sha>`` (the hash of the class's
+    KERNEL_SOURCES); None if absent or stale."""
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None
-    sha = csrc_sha()
+    sha = csrc_sha(KERNEL_SOURCES.get((kernel_class, precision)))
     for name in os.listdir(pdir):
         if not name.endswith((".md", ".txt")):
             continue
