@@ -64,33 +64,51 @@ WD_DEV void transport_at(const E* __restrict__ x, const float* __restrict__ link
   if constexpr (D >= 5) colour_mult<-1>(links + 2 * ((size_t)(D - 5) * 9 * V + sn), V, v);
 }
 
-template <int CIN, int COUT, int D, typename E>
-WD_DEV void layer_dir(const E* __restrict__ in, const float* __restrict__ links,
-                      const float2* Ws, const Geom& g, int s, const int c[4], int r, int L,
-                      Cx<float> acc[COUT][12]) {
-  const size_t chan = (size_t)12 * g.V * L;   // elements per channel
+// T_d psi at site s for one channel, the direction d (0..8) given at run time, so that one rolled
+// loop over d serves all nine (an unrolled body of nine directions takes every register and spills).
+template <typename E>
+WD_DEV void transport_rt(const E* __restrict__ x, const float* __restrict__ links, const Geom& g,
+                         int s, const int c[4], int r, int L, int d, Cx<float> v[12]) {
+  const size_t V = (size_t)g.V;
+  int sn = s;
+  const int mu = (d - 1) & 3;
+  const bool fwd = d <= 4;
+  if (d > 0) {
+    const int cm = mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
+    const int dm = mu == 0 ? g.d[0] : mu == 1 ? g.d[1] : mu == 2 ? g.d[2] : g.d[3];
+    const int st = mu == 0 ? g.stride[0] : mu == 1 ? g.stride[1] : mu == 2 ? g.stride[2] : g.stride[3];
+    sn = fwd ? (cm == dm - 1 ? s - (dm - 1) * st : s + st) : (cm == 0 ? s + (dm - 1) * st : s - st);
+  }
 #pragma unroll
-  for (int ci = 0; ci < CIN; ++ci) {
-    Cx<float> v[12];
-    transport_at<D>(in + ci * chan, links, g, s, c, r, L, v);
+  for (int k = 0; k < 12; ++k) v[k] = lp::ld1(x + ((size_t)k * V + sn) * L + r);
+  if (d == 0) return;
+  // W = U_mu(s) forward, U_mu(s - mu)^H backward: entry (a, b) = u[a][b] or conj(u[b][a])
+  const float* U = links + 2 * ((size_t)mu * 9 * V + (fwd ? s : sn));
+  Cx<float> m[3][3];
 #pragma unroll
-    for (int co = 0; co < COUT; ++co) {
-      const float2* w = Ws + ((D * COUT + co) * CIN + ci) * 16;
+  for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const float2 wv = w[sp * 4 + t];
-          const Cx<float> wc = {wv.x, wv.y};
-#pragma unroll
-          for (int a = 0; a < 3; ++a) acc[co][sp * 3 + a] = cfma(wc, v[t * 3 + a], acc[co][sp * 3 + a]);
-        }
+    for (int b = 0; b < 3; ++b) {
+      const Cx<float> t = ldc(U + 2 * (size_t)((fwd ? a * 3 + b : b * 3 + a)) * V);
+      m[a][b] = fwd ? t : conj(t);
     }
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp) {
+    Cx<float> w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Cx<float> acc = czero<float>();
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc = cfma(m[a][b], v[sp * 3 + b], acc);
+      w[a] = acc;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[sp * 3 + a] = w[a];
   }
 }
 
 template <int CIN, int COUT, typename E>
-__global__ void __launch_bounds__(NET_THREADS)
+__global__ void __launch_bounds__(NET_THREADS, 3)
 net_layer_kernel(const E* __restrict__ in, E* __restrict__ out,
                  const float* __restrict__ links, const float2* __restrict__ W, Geom g, int L) {
   __shared__ float2 Ws[9 * COUT * CIN * 16];
@@ -107,15 +125,29 @@ net_layer_kernel(const E* __restrict__ in, E* __restrict__ out,
   for (int co = 0; co < COUT; ++co)
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[co][k] = czero<float>();
-  layer_dir<CIN, COUT, 0, E>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 1, E>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 2, E>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 3, E>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 4, E>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 5, E>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 6, E>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 7, E>(in, links, Ws, g, s, c, r, L, acc);
-  layer_dir<CIN, COUT, 8, E>(in, links, Ws, g, s, c, r, L, acc);
+  const size_t chan_in = (size_t)12 * g.V * L;
+#pragma unroll 1
+  for (int d = 0; d < 9; ++d) {
+#pragma unroll
+    for (int ci = 0; ci < CIN; ++ci) {
+      Cx<float> v[12];
+      transport_rt(in + ci * chan_in, links, g, s, c, r, L, d, v);
+#pragma unroll
+      for (int co = 0; co < COUT; ++co) {
+        const float2* w = Ws + ((d * COUT + co) * CIN + ci) * 16;
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const float2 wv = w[sp * 4 + t];
+            const Cx<float> wc = {wv.x, wv.y};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+              acc[co][sp * 3 + a] = cfma(wc, v[t * 3 + a], acc[co][sp * 3 + a]);
+          }
+      }
+    }
+  }
   const size_t V = (size_t)g.V;
   const size_t chan = (size_t)12 * V * L;
 #pragma unroll
