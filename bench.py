@@ -567,6 +567,83 @@ def grid8_workload(args):
     return 0 if ok else 1
 
 
+# ---------------------------------------------------------------- the learned preconditioner
+NET_LAYERS, NET_HIDDEN = 4, 4
+
+
+def net_flop(layers: int, hidden: int) -> int:
+    """Flop per site and RHS of one network application: every layer transports each input channel
+    along the 8 hops (4 spins x a 3x3 complex link: 36 complex multiply-adds, 288 flop) and mixes
+    every (output, input) channel pair in each of the 9 directions (a 4x4 complex spin matrix on 3
+    colours: 48 complex multiply-adds, 384 flop)."""
+    from paper_0907_3261_gb300 import inputs as I
+    ch = I.network_channels(layers, hidden)
+    pairs = zip(ch[:-1], ch[1:])
+    return sum(cin * 8 * 288 + cin * cout * 9 * 384 for cin, cout in pairs)
+
+
+def net_workload(args):
+    """One application G = N(R) of the learned gauge-covariant preconditioner (4 layers, channels
+    1-4-4-4-1) on the bench lattice (16^3 x 32, L = 12, the bench's links), with weights from the
+    seeded initialisation plus noise 0.1; FP32 activations (the value) and BF16 activations.
+    One application converts R to the FP32 channel layout, runs the 4 layer kernels and converts
+    back (6 launches), moving ~4.8 GB of activations and blocks, far more than L2."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0907_3261_gb300 as wd
+    from paper_0907_3261_gb300 import inputs as I
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    links = torch.from_numpy(I.random_links(DIMS, LINK_EPS, seed=0)).to(dev)
+    ctx = wd.wd_create(links, DIMS, KAPPA, CSW)
+    net = wd.wd_net_create(NET_LAYERS, NET_HIDDEN,
+                           I.network_weights(NET_LAYERS, NET_HIDDEN, seed=0, noise=0.1))
+    R = torch.from_numpy(I.z4_noise(DIMS, L_RHS, seed=1)).to(dev)
+    G = torch.empty_like(R)
+    stream = torch.cuda.current_stream(dev)
+    times = {}
+    clocks = None
+    for bf16 in (False, True):
+        for _ in range(args.warmup):
+            wd.wd_net_apply(ctx, net, R, G, bf16=bf16, stream=stream)
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(gpu_id_for_smi(torch, dev)) if not bf16 else None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            wd.wd_net_apply(ctx, net, R, G, bf16=bf16, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if sampler is not None:
+            clocks = sampler.stop()
+        times["bf16" if bf16 else "fp32"] = e0.elapsed_time(e1) / args.steps
+    ok = bool(torch.isfinite(G).all().item())
+    V = 1
+    for d in DIMS:
+        V *= d
+    flop = net_flop(NET_LAYERS, NET_HIDDEN) * V * L_RHS
+    props = torch.cuda.get_device_properties(dev)
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = 2 * alu_peaks(props.multi_processor_count, mhz)["fp32_lane_tops"]   # FMA = 2 flop
+    achieved = flop / (times["fp32"] * 1e-3) / 1e12
+    out = {"metric": "learned preconditioner application time (16^3x32, L=12)",
+           "value": round(times["fp32"], 4), "unit": "ms", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(times["fp32"], 4),
+           "higher_is_better": False, "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "network application: 4 layers, channels 1-4-4-4-1, 16^3x32, "
+                                  "L=12, activations > L2",
+                      "flop_per_site_rhs": net_flop(NET_LAYERS, NET_HIDDEN)},
+           "bf16_activations_ms": round(times["bf16"], 4),
+           "gpu_launches": (NET_LAYERS + 2) * args.steps,
+           "roofline": {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2),
+                        "unit": "TFLOP/s", "frac": round(achieved / peak, 3), "traffic": None,
+                        "peak_kind": "derived: SMs x 128 FP32 lanes x 2 flop x sampled SM clock"},
+           "clocks": clocks, "status": "ok" if ok else "FAILED"}
+    print(json.dumps(out), flush=True)
+    return 0 if ok else 1
+
+
 def gpu_small_solves(wd, I, dev, prec):
     """The same c1 and c2 solves on the GPU (default form), for the side-by-side baseline."""
     import torch
@@ -616,9 +693,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-mix", default="stated", choices=list(BATCH_MIXES),
                     help="preconditioners of the batch24 workload")
-    ap.add_argument("--workload", default="tts", choices=["tts", "batch24", "grid8"],
+    ap.add_argument("--workload", default="tts", choices=["tts", "batch24", "grid8", "net16"],
                     help="tts: the time-to-solution line; batch24: 24 solves in one CUDA graph; "
-                         "grid8: the FP64 method's kappa scan and L x j grid on 8^3x16")
+                         "grid8: the FP64 method's kappa scan and L x j grid on 8^3x16; net16: "
+                         "one application of the learned preconditioner on 16^3x32, L = 12")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -628,6 +706,8 @@ def main():
         return batch_workload(args)
     if args.workload == "grid8":
         return grid8_workload(args)
+    if args.workload == "net16":
+        return net_workload(args)
 
     import numpy as np
     import torch

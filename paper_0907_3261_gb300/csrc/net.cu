@@ -22,7 +22,7 @@
 
 namespace {
 
-constexpr int NET_THREADS = 128;
+constexpr int NET_THREADS = 64;
 constexpr int WG_THREADS = 256;
 constexpr int WG_PAIRS = 32;        // (site, rhs) pairs per chunk of the weight-gradient kernel
 
@@ -64,11 +64,19 @@ WD_DEV void transport_at(const E* __restrict__ x, const float* __restrict__ link
   if constexpr (D >= 5) colour_mult<-1>(links + 2 * ((size_t)(D - 5) * 9 * V + sn), V, v);
 }
 
+// acc + a b for complex values held as (re, im) lane pairs, with a given as the pairs
+// (a.re, a.re) and (-a.im, a.im) and b also as (b.im, b.re): two paired FMAs, rounded in the same
+// order as cfma (re: (acc + a.re b.re) - a.im b.im; im: (acc + a.re b.im) + a.im b.re).
+WD_DEV float2 cfma_pair(float2 arr, float2 nai, float2 b, float2 bsw, float2 acc) {
+  return __ffma2_rn(nai, bsw, __ffma2_rn(arr, b, acc));
+}
+
 // T_d psi at site s for one channel, the direction d (0..8) given at run time, so that one rolled
 // loop over d serves all nine (an unrolled body of nine directions takes every register and spills).
+// The result is returned as lane pairs v and their swapped copies vs, ready for cfma_pair.
 template <typename E>
 WD_DEV void transport_rt(const E* __restrict__ x, const float* __restrict__ links, const Geom& g,
-                         int s, const int c[4], int r, int L, int d, Cx<float> v[12]) {
+                         int s, const int c[4], int r, int L, int d, float2 v[12], float2 vs[12]) {
   const size_t V = (size_t)g.V;
   int sn = s;
   const int mu = (d - 1) & 3;
@@ -80,39 +88,50 @@ WD_DEV void transport_rt(const E* __restrict__ x, const float* __restrict__ link
     sn = fwd ? (cm == dm - 1 ? s - (dm - 1) * st : s + st) : (cm == 0 ? s + (dm - 1) * st : s - st);
   }
 #pragma unroll
-  for (int k = 0; k < 12; ++k) v[k] = lp::ld1(x + ((size_t)k * V + sn) * L + r);
-  if (d == 0) return;
-  // W = U_mu(s) forward, U_mu(s - mu)^H backward: entry (a, b) = u[a][b] or conj(u[b][a])
-  const float* U = links + 2 * ((size_t)mu * 9 * V + (fwd ? s : sn));
-  Cx<float> m[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const Cx<float> t = ldc(U + 2 * (size_t)((fwd ? a * 3 + b : b * 3 + a)) * V);
-      m[a][b] = fwd ? t : conj(t);
-    }
-#pragma unroll
-  for (int sp = 0; sp < 4; ++sp) {
-    Cx<float> w[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      Cx<float> acc = czero<float>();
-#pragma unroll
-      for (int b = 0; b < 3; ++b) acc = cfma(m[a][b], v[sp * 3 + b], acc);
-      w[a] = acc;
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) v[sp * 3 + a] = w[a];
+  for (int k = 0; k < 12; ++k) {
+    const Cx<float> t = lp::ld1(x + ((size_t)k * V + sn) * L + r);
+    v[k] = make_float2(t.re, t.im);
   }
+  if (d > 0) {
+    // W = U_mu(s) forward, U_mu(s - mu)^H backward: entry (a, b) = u[a][b] or conj(u[b][a])
+    const float* U = links + 2 * ((size_t)mu * 9 * V + (fwd ? s : sn));
+    float2 w[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w[k] = make_float2(0.f, 0.f);
+    // each link entry is loaded, paired and used on the four spins before the next one
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const Cx<float> t = ldc(U + 2 * (size_t)((fwd ? a * 3 + b : b * 3 + a)) * V);
+        const float im = fwd ? t.im : -t.im;
+        const float2 mrr = make_float2(t.re, t.re), mni = make_float2(-im, im);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+          const float2 x2 = v[sp * 3 + b];
+          w[sp * 3 + a] = cfma_pair(mrr, mni, x2, make_float2(x2.y, x2.x), w[sp * 3 + a]);
+        }
+      }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = w[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) vs[k] = make_float2(v[k].y, v[k].x);
 }
 
+// One gauge-covariant layer: out_co(x) = sum_d sum_ci W[d][co][ci] (T_d in_ci)(x), one thread per
+// (site, RHS). The weights sit in shared memory as (w.re, w.re, -w.im, w.im), the direction and
+// input-channel loops are rolled (an unrolled body overflows the instruction cache) and the output
+// channels' accumulators stay in registers.
 template <int CIN, int COUT, typename E>
-__global__ void __launch_bounds__(NET_THREADS, 3)
+__global__ void __launch_bounds__(NET_THREADS, 5)
 net_layer_kernel(const E* __restrict__ in, E* __restrict__ out,
                  const float* __restrict__ links, const float2* __restrict__ W, Geom g, int L) {
-  __shared__ float2 Ws[9 * COUT * CIN * 16];
-  for (int e = threadIdx.x; e < 9 * COUT * CIN * 16; e += blockDim.x) Ws[e] = W[e];
+  __shared__ float4 Ws[9 * COUT * CIN * 16];
+  for (int e = threadIdx.x; e < 9 * COUT * CIN * 16; e += blockDim.x) {
+    const float2 w = W[e];
+    Ws[e] = make_float4(w.x, w.x, -w.y, w.y);
+  }
   __syncthreads();
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= g.V * L) return;
@@ -120,30 +139,31 @@ net_layer_kernel(const E* __restrict__ in, E* __restrict__ out,
   const int r = tid - s * L;
   int c[4];
   site_coords(g, s, c);
-  Cx<float> acc[COUT][12];
+  float2 acc[COUT][12];
 #pragma unroll
   for (int co = 0; co < COUT; ++co)
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[co][k] = czero<float>();
+    for (int k = 0; k < 12; ++k) acc[co][k] = make_float2(0.f, 0.f);
   const size_t chan_in = (size_t)12 * g.V * L;
 #pragma unroll 1
   for (int d = 0; d < 9; ++d) {
-#pragma unroll
+#pragma unroll 1
     for (int ci = 0; ci < CIN; ++ci) {
-      Cx<float> v[12];
-      transport_rt(in + ci * chan_in, links, g, s, c, r, L, d, v);
+      float2 v[12], vs[12];
+      transport_rt(in + ci * chan_in, links, g, s, c, r, L, d, v, vs);
 #pragma unroll
       for (int co = 0; co < COUT; ++co) {
-        const float2* w = Ws + ((d * COUT + co) * CIN + ci) * 16;
+        const float4* w = Ws + ((d * COUT + co) * CIN + ci) * 16;
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
-            const float2 wv = w[sp * 4 + t];
-            const Cx<float> wc = {wv.x, wv.y};
+            const float4 wv = w[sp * 4 + t];
+            const float2 wrr = make_float2(wv.x, wv.y), wni = make_float2(wv.z, wv.w);
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-              acc[co][sp * 3 + a] = cfma(wc, v[t * 3 + a], acc[co][sp * 3 + a]);
+              acc[co][sp * 3 + a] = cfma_pair(wrr, wni, v[t * 3 + a], vs[t * 3 + a],
+                                              acc[co][sp * 3 + a]);
           }
       }
     }
@@ -153,7 +173,8 @@ net_layer_kernel(const E* __restrict__ in, E* __restrict__ out,
 #pragma unroll
   for (int co = 0; co < COUT; ++co)
 #pragma unroll
-    for (int k = 0; k < 12; ++k) lp::st1(out + co * chan + ((size_t)k * V + s) * L + r, acc[co][k]);
+    for (int k = 0; k < 12; ++k)
+      lp::st1(out + co * chan + ((size_t)k * V + s) * L + r, Cx<float>{acc[co][k].x, acc[co][k].y});
 }
 
 // W^adj[d'][c][c'] = W[d][c'][c]^H with d' the opposite direction of d (0 stays 0).

@@ -31,6 +31,15 @@ def test_operation_counts():
     assert bench.FLOP_APPLY == 1320 + 504
 
 
+def test_network_flop_count():
+    # one 1 -> 1 layer: one input channel transported along 8 hops (4 spins x 9 complex
+    # multiply-adds x 8 flop) and one channel pair mixed in 9 directions (4 x 4 spin entries x 3
+    # colours x 8 flop)
+    assert bench.net_flop(1, 1) == 8 * 4 * 9 * 8 + 9 * 16 * 3 * 8
+    # 1 -> 4 -> 4 -> 4 -> 1: 13 transported input channels, 40 channel pairs
+    assert bench.net_flop(4, 4) == 13 * 8 * 288 + 40 * 9 * 384
+
+
 def test_derived_alu_peaks():
     p = bench.alu_peaks(152, 2070.0)
     assert p["fp32_lane_tops"] == pytest.approx(152 * 128 * 2.07e9 / 1e12)
