@@ -49,7 +49,9 @@ def held_out_loss(wd, net, pairs):
 
 
 def compare(wd, I, torch, net, dims, kappa, csw, seeds, L, eps, j, dev, maxit=3000):
-    """Iterations and time of block BiCGGR with each preconditioner on held-out configurations."""
+    """Iterations and time of block BiCGGR with each preconditioner on held-out configurations:
+    FP64, FP32 and double-float Jacobi (the last with double-float direction recurrences), the
+    network with FP64 or double-float direction recurrences, and no preconditioner."""
     rows = []
     for s in seeds:
         links = torch.from_numpy(I.random_links(dims, eps, seed=s)).to(dev)
@@ -57,7 +59,10 @@ def compare(wd, I, torch, net, dims, kappa, csw, seeds, L, eps, j, dev, maxit=30
         B = torch.from_numpy(I.z4_noise(dims, L, seed=2000 + s)).to(dev)
         row = {"seed": s}
         for name, kw in (("jacobi_fp64", dict(j=j)), ("jacobi_fp32", dict(j=j, precision=1)),
-                         ("network", dict(j=j, net=net)), ("none", dict(j=0))):
+                         ("jacobi_df_dirs", dict(j=j, precision=5)),
+                         ("network", dict(j=j, net=net)),
+                         ("network_df_dirs", dict(j=j, net=net, precision=2)),
+                         ("none", dict(j=0))):
             wd.bbicggr_solve(ctx, B, maxit=maxit, **kw)                  # warm-up (autotuning)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
