@@ -60,6 +60,24 @@ def test_net_forward_matches_oracle(wd, layers, hidden):
     assert all(np.array_equal(a, b) for a, b in zip(wd.wd_net_get_weights(net), W))
 
 
+def test_net_full_size_columns_element_wise(wd):
+    """The bench lattice in the launch shape bench.py --workload net16 times (16^3 x 32, L = 12,
+    4 layers, 4 hidden channels): columns 0 and 11 of the GPU's N(R) against the oracle run on
+    each column alone, element by element relative to the column's largest entry."""
+    dims, L = (16, 16, 16, 32), 12
+    U = I.random_links(dims, 0.2, seed=0)
+    W = [w.astype(np.complex64).astype(np.complex128)
+         for w in I.network_weights(4, 4, seed=0, noise=0.1)]
+    R = I.z4_noise(dims, L, seed=1)
+    ctx = wd.wd_create(dev(U), dims, 0.134, 1.0)
+    net = wd.wd_net_create(4, 4, W)
+    G = host(wd.wd_net_apply(ctx, net, dev(R)))
+    lat = O.Lattice(dims)
+    for r in (0, L - 1):
+        Y = N.forward(U, lat, W, np.ascontiguousarray(R[..., r:r + 1]))[0][..., 0]
+        assert np.abs(G[..., r] - Y).max() <= NET_TOL * np.abs(Y).max()
+
+
 @pytest.mark.parametrize("layers,hidden", [(4, 4), (3, 2)])
 def test_net_forward_bf16_activations(wd, layers, hidden):
     """BF16-stored activations (inference): the input and every layer's output are rounded to
