@@ -136,11 +136,12 @@ WD_DEV void x3_add_sm(SumRef t, int idx, const X3& w) {
 // added to the upper spin SP and, through G_mu^H, to one lower spin.  The spin tables of
 // gamma_down / gamma_up (spin.cuh) enter at run time, so that one loop body serves all eight
 // hops: (G_mu d)_SP = phase * d_pi and G_mu^H sends w_SP to lower spin t with another phase
-// (phases 0 = +1, 1 = +i, 2 = -1, 3 = -i).  xp points at the neighbour's spinor, U at the
-// link's three-level copy ([level][entry], each entry (re, re, im, im)).
-template <int SP>
-WD_DEV void hop_x3_spin(const double* __restrict__ xp, const float4* __restrict__ U, int L, int k,
-                        int mu, int dir, SumRef sums, float2 m1) {
+// (phases 0 = +1, 1 = +i, 2 = -1, 3 = -i).  SP is a run-time value as well (the caller loops over
+// the two upper spins): one spin's body is half the code, which keeps the hop loop out of
+// instruction-fetch stalls and spills.  xp points at the neighbour's spinor, U at the link's
+// three-level copy ([level][entry], each entry (re, re, im, im)).
+WD_DEV void hop_x3_spin(int SP, const double* __restrict__ xp, const float4* __restrict__ U, int L,
+                        int k, int mu, int dir, SumRef sums, float2 m1) {
   const int pi = mu <= 1 ? 1 - SP : SP;
   // 2-bit tables over mu = 0..3: gamma_down's phase (SP 0: 3, 2, 3, 0; SP 1: 3, 0, 1, 0) and
   // gamma_up's (SP 0: 1, 2, 1, 0; SP 1: 1, 0, 3, 0); gamma_up's target spin equals pi
@@ -247,8 +248,8 @@ dslash_x3_kernel(const double* __restrict__ x, double* __restrict__ y,
                            : (cm == 0 ? s + (dm - 1) * st : s - st);
     const double* xp = x + 2 * ((size_t)sn * 12 * L + r);
     const float4* U = lx + (size_t)((dir > 0 ? s : sn) * 4 + mu) * 27;
-    hop_x3_spin<0>(xp, U, L, k, mu, dir, sums, m1);
-    hop_x3_spin<1>(xp, U, L, k, mu, dir, sums, m1);
+#pragma unroll 1
+    for (int sp = 0; sp < 2; ++sp) hop_x3_spin(sp, xp, U, L, k, mu, dir, sums, m1);
   }
 
   // H x = 2^k ((S1 - XS1) + (S2 - XS2) + S3): the first two levels join exactly in FP64, S3 and
