@@ -22,6 +22,8 @@
 
 namespace {
 
+// 64-thread CTAs: the 4->4 layer's 168 registers a thread and 36.9 KB of staged weights fit six
+// CTAs (12 warps) per SM, where 128-thread CTAs fit two or three.
 constexpr int NET_THREADS = 64;
 constexpr int WG_THREADS = 256;
 constexpr int WG_PAIRS = 32;        // (site, rhs) pairs per chunk of the weight-gradient kernel
